@@ -1,0 +1,207 @@
+"""Seeded synthetic inputs for rotational alignment (Gaussian-blob volumes).
+
+This module only *makes inputs*.  It holds none of the alignment method's
+arithmetic (no spherical harmonics, no Wigner functions, no correlation): the
+oracle and the CUDA library both consume the float32 volumes it returns.
+
+Recipe (one particle = one (template, particle) pair, each from its own seed):
+
+* template ``h``: a sum of isotropic Gaussian blobs ``a*exp(-|x-c|^2/(2 sigma^2))``
+  evaluated at voxel centres; blob centres uniform in a ball of the given
+  radius around the box centre ``c0 = N/2`` (rejection sampling), amplitudes
+  ``U[0.5, 1]``;
+* ground truth rotation ``R*``: a normalised 4-vector of standard normals
+  (a Haar-random unit quaternion);
+* clean particle ``s(x) = h(R*^T (x - c0) + c0)`` by trilinear interpolation of
+  the template (or, with ``exact_rotation=True``, the blobs re-rendered at the
+  rotated centres, which is the exact rotation of a sum of isotropic Gaussians);
+* noise: i.i.d. Gaussian with variance ``mean_box(s^2) / SNR``;
+* optional missing wedge (tilt axis y, beam z): keep the Fourier samples with
+  ``|k_z| <= tan(wedge) * |k_x|`` plus the zero-frequency sample.
+
+This stands in for the paper's particle model ``f = g* o h + noise``
+(Section 5.1) on the subtomogram shapes of its experiments.  Volumes are C-order
+``[z][y][x]``; voxel ``[k][j][i]`` sits at position ``(x, y, z) = (i, j, k)``.
+
+Random draws come from ``numpy.random.SeedSequence(base_seed).spawn(B)``, one
+child per particle, so results do not depend on the device that renders them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+__all__ = [
+    "Workload", "WORKLOADS", "haar_rotation", "blob_params", "render_blobs",
+    "rotate_trilinear", "apply_missing_wedge", "make_batch",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A synthetic workload: volume recipe plus the alignment parameters."""
+    name: str
+    B: int
+    N: int
+    n_blobs: int
+    sigma: float
+    ball_radius: float
+    snr: float
+    wedge_deg: Optional[float]
+    n_shells: int
+    L_sched: Sequence[int]
+    L0: int
+    K: int
+    P: int
+    M_iter: int
+    base_seed: int
+    shared_template: bool = False
+
+    @property
+    def r_max(self) -> float:
+        return self.N / 2 - 1.0
+
+    @property
+    def L_final(self) -> int:
+        return int(self.L_sched[-1])
+
+
+# The two single-GPU workloads: a small FP64 case the oracle finishes in
+# seconds, and the 1024-particle 64^3 batch the throughput metric is quoted on.
+WORKLOADS = {
+    "small32": Workload("small32", B=1, N=32, n_blobs=16, sigma=1.5, ball_radius=12.0,
+                        snr=0.5, wedge_deg=None, n_shells=12, L_sched=(8, 12, 16),
+                        L0=8, K=2, P=8, M_iter=3, base_seed=20260316),
+    "batch64": Workload("batch64", B=1024, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
+                        snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
+                        L0=8, K=2, P=16, M_iter=3, base_seed=20260317),
+    "grad64": Workload("grad64", B=512, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
+                       snr=0.2, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
+                       L0=8, K=2, P=16, M_iter=3, base_seed=20260320, shared_template=True),
+}
+
+
+def haar_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random rotation matrix from a normalised Gaussian quaternion."""
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def blob_params(rng: np.random.Generator, n_blobs: int, ball_radius: float):
+    """Blob centre offsets (uniform in a ball, rejection sampled) and amplitudes."""
+    cs = []
+    while len(cs) < n_blobs:
+        p = rng.uniform(-ball_radius, ball_radius, size=3)
+        if p @ p <= ball_radius * ball_radius:
+            cs.append(p)
+    amps = rng.uniform(0.5, 1.0, size=n_blobs)
+    return np.array(cs), amps
+
+
+def render_blobs(N: int, offsets: np.ndarray, amps: np.ndarray, sigma: float,
+                 device="cpu") -> torch.Tensor:
+    """Sum of isotropic Gaussians at voxel centres; returns float64 [z][y][x].
+
+    An isotropic Gaussian factorises over x, y, z, so the volume is a sum of
+    outer products of three 1-D profiles.
+    """
+    c0 = N / 2
+    grid = torch.arange(N, dtype=torch.float64, device=device) - c0
+    off = torch.as_tensor(offsets, dtype=torch.float64, device=device)
+    a = torch.as_tensor(amps, dtype=torch.float64, device=device)
+    g = torch.exp(-(grid[None, None, :] - off[:, :, None]) ** 2 / (2 * sigma * sigma))  # [b][xyz][N]
+    return torch.einsum("b,bz,by,bx->zyx", a, g[:, 2], g[:, 1], g[:, 0])
+
+
+def rotate_trilinear(vol: torch.Tensor, R: np.ndarray) -> torch.Tensor:
+    """out(x) = vol(R^T (x - c0) + c0) by trilinear interpolation, zero outside."""
+    N = vol.shape[-1]
+    dev = vol.device
+    c0 = N / 2
+    Rt = torch.as_tensor(R, dtype=torch.float64, device=dev).T
+    ax = torch.arange(N, dtype=torch.float64, device=dev) - c0
+    zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
+    pts = torch.stack([xx, yy, zz], -1).reshape(-1, 3) @ Rt.T + c0   # (x, y, z)
+    i0 = torch.floor(pts).long()
+    fr = pts - i0
+    out = torch.zeros(pts.shape[0], dtype=vol.dtype, device=dev)
+    flat = vol.reshape(-1)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                ix, iy, iz = i0[:, 0] + dx, i0[:, 1] + dy, i0[:, 2] + dz
+                w = ((fr[:, 0] if dx else 1 - fr[:, 0]) * (fr[:, 1] if dy else 1 - fr[:, 1])
+                     * (fr[:, 2] if dz else 1 - fr[:, 2]))
+                ok = (ix >= 0) & (ix < N) & (iy >= 0) & (iy < N) & (iz >= 0) & (iz < N)
+                lin = (iz.clamp(0, N - 1) * N + iy.clamp(0, N - 1)) * N + ix.clamp(0, N - 1)
+                out += torch.where(ok, w * flat[lin], torch.zeros_like(w))
+    return out.reshape(N, N, N)
+
+
+def apply_missing_wedge(vol: torch.Tensor, wedge_deg: float) -> torch.Tensor:
+    """Zero the Fourier samples outside a +-wedge_deg tilt range (axis y, beam z)."""
+    N = vol.shape[-1]
+    F = torch.fft.fftn(vol)
+    k = torch.fft.fftfreq(N, device=vol.device, dtype=torch.float64)
+    kz, ky, kx = torch.meshgrid(k, k, k, indexing="ij")
+    keep = kz.abs() <= math.tan(math.radians(wedge_deg)) * kx.abs() + 1e-12
+    keep |= (kz == 0) & (kx == 0) & (ky == 0)
+    return torch.fft.ifftn(F * keep).real
+
+
+def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu",
+               exact_rotation: bool = False, noise: bool = True):
+    """Generate particles ``start .. start+B-1`` of workload ``w``.
+
+    Returns dict with ``templates`` (float32 [Bt][N][N][N], Bt = 1 when the
+    workload shares one template, else B), ``particles`` (float32 [B][N][N][N]),
+    ``R_true`` (float64 [B][3][3]).
+    """
+    B = w.B if B is None else B
+    seeds = np.random.SeedSequence(w.base_seed).spawn(start + B)[start:]
+    N = w.N
+    parts = torch.empty((B, N, N, N), dtype=torch.float32, device=device)
+    temps = []
+    Rs = np.empty((B, 3, 3))
+    shared = None
+    if w.shared_template:
+        trng = np.random.default_rng(np.random.SeedSequence(w.base_seed + 7919))
+        offs, amps = blob_params(trng, w.n_blobs, w.ball_radius)
+        shared = (offs, amps, render_blobs(N, offs, amps, w.sigma, device))
+        temps.append(shared[2].float())
+    for b, ss in enumerate(seeds):
+        rng = np.random.default_rng(ss)
+        if shared is None:
+            offs, amps = blob_params(rng, w.n_blobs, w.ball_radius)
+            h = render_blobs(N, offs, amps, w.sigma, device)
+            temps.append(h.float())
+        else:
+            offs, amps, h = shared
+        R = haar_rotation(rng)
+        Rs[b] = R
+        if exact_rotation:
+            s = render_blobs(N, offs @ R.T, amps, w.sigma, device)
+        else:
+            s = rotate_trilinear(h, R)
+        if noise and w.snr is not None and w.snr > 0:
+            var = float((s * s).mean()) / w.snr
+            eta = rng.standard_normal((N, N, N), dtype=np.float32)
+            s = s + math.sqrt(var) * torch.from_numpy(eta).to(device=device, dtype=s.dtype)
+        if w.wedge_deg is not None:
+            s = apply_missing_wedge(s, w.wedge_deg)
+        parts[b] = s.float()
+    return {
+        "templates": torch.stack(temps),
+        "particles": parts,
+        "R_true": Rs,
+    }

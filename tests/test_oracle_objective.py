@@ -1,0 +1,233 @@
+"""Pins for the oracle's correlation coefficients, C_L and its derivatives,
+the SOFFT grid, candidate selection and the Newton march."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+RNG = np.random.default_rng(21)
+
+
+def rand_coef(L, S):
+    a = np.zeros((S, O.lm_size(L)), complex)
+    for s in range(S):
+        for l in range(L + 1):
+            for m in range(l + 1):
+                a[s, O.lm_index(l, m)] = RNG.normal() + (1j * RNG.normal() if m else 0)
+    return a
+
+
+def full_orders(a_l, l):
+    """coefficients for n = -l..l of one degree from the m >= 0 half."""
+    return np.array([a_l[O.lm_index(l, n)] if n >= 0 else (-1) ** n * np.conj(a_l[O.lm_index(l, -n)])
+                     for n in range(-l, l + 1)])
+
+
+def test_correlation_equals_brute_force_quadrature():
+    """C_L(g) from c^l_mn equals sum_s w_s sum_jk w_j (2pi/n_phi) f_L(r_s w) h_L(r_s g^{-1} w),
+    the ball inner product <f, g o h> of the bandlimited shell functions."""
+    L, S, R = 5, 3, 6.0
+    f, h = rand_coef(L, S), rand_coef(L, S)
+    c = O.correlate(f, h, S, R, L)
+    r, ws = O.radial_nodes(S, R)
+    x, w = O.gauss_legendre(L + 1)
+    nphi = 2 * L + 2
+    for _ in range(3):
+        g = (RNG.uniform(0, 2 * math.pi), RNG.uniform(0, math.pi), RNG.uniform(0, 2 * math.pi))
+        Rg = O.euler_to_matrix(*g)
+        tot = 0.0
+        for s in range(S):
+            for j in range(L + 1):
+                th = math.acos(x[j])
+                for k in range(nphi):
+                    ph = 2 * math.pi * k / nphi
+                    v = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+                    u = Rg.T @ v
+                    hv = O.sh_synthesize(h[s], L, math.acos(max(-1, min(1, u[2]))), math.atan2(u[1], u[0]))
+                    tot += ws[s] * w[j] * (2 * math.pi / nphi) * O.sh_synthesize(f[s], L, th, ph) * hv
+        C, im = O.objective(c, L, *g)
+        assert abs(C - tot) < 1e-10 * abs(tot)
+        assert abs(im) < 1e-12 * abs(tot)
+
+
+def test_parseval_identity_is_the_maximum():
+    L, S, R = 6, 4, 8.0
+    f = rand_coef(L, S)
+    c = O.correlate(f, f, S, R, L)
+    r, ws = O.radial_nodes(S, R)
+    energy = sum(ws[s] * sum(np.sum(np.abs(full_orders(f[s], l)) ** 2) for l in range(L + 1))
+                 for s in range(S))
+    C0, im = O.objective(c, L, 0.0, 0.0, 0.0)
+    assert abs(C0 - energy) < 1e-12 * energy and abs(im) < 1e-12 * energy
+    for _ in range(50):
+        g = (RNG.uniform(0, 2 * math.pi), RNG.uniform(0, math.pi), RNG.uniform(0, 2 * math.pi))
+        assert O.objective(c, L, *g)[0] <= C0 + 1e-12 * energy
+
+
+def test_rank_bound_and_rotation_of_template():
+    """Appendix A.6: rank(A_l) <= #radial terms; rotating h by g in coefficient
+    space (b -> D^l(g) b) turns A_l into A_l D^l(g)^*."""
+    L, S, R = 8, 3, 5.0
+    f, h = rand_coef(L, S), rand_coef(L, S)
+    c = O.correlate(f, h, S, R, L)
+    g = (0.7, 1.1, 4.0)
+    h_rot = np.zeros_like(h)
+    for s in range(S):
+        for l in range(L + 1):
+            hr = O.wigner_D(l, *g) @ full_orders(h[s], l)
+            for m in range(l + 1):
+                h_rot[s, O.lm_index(l, m)] = hr[m + l]
+    c_rot = O.correlate(f, h_rot, S, R, L)
+    for l in range(L + 1):
+        o = O.c_index(l, -l, -l)
+        A = c[o:o + (2 * l + 1) ** 2].reshape(2 * l + 1, 2 * l + 1)
+        Ar = c_rot[o:o + (2 * l + 1) ** 2].reshape(2 * l + 1, 2 * l + 1)
+        sv = np.linalg.svd(A, compute_uv=False)
+        assert np.sum(sv > 1e-10 * sv[0]) <= min(2 * l + 1, S)
+        assert np.abs(Ar - A @ O.wigner_D(l, *g).conj().T).max() < 1e-11 * np.abs(A).max()
+
+
+def test_gradient_and_hessian_match_central_differences():
+    L, S, R = 12, 3, 6.0
+    f, h = rand_coef(L, S), rand_coef(L, S)
+    c = O.correlate(f, h, S, R, L)
+    eps = 1e-5
+    for _ in range(3):
+        t = np.array([RNG.uniform(0, 2 * math.pi), RNG.uniform(0.3, 2.8), RNG.uniform(0, 2 * math.pi)])
+        C, g, H, _ = O.objective(c, L, *t, derivs=True)
+        fd_g = np.zeros(3)
+        fd_H = np.zeros((3, 3))
+        for i in range(3):
+            e = np.zeros(3); e[i] = eps
+            Cp, gp, _, _ = O.objective(c, L, *(t + e), derivs=True)
+            Cm, gm, _, _ = O.objective(c, L, *(t - e), derivs=True)
+            fd_g[i] = (Cp - Cm) / (2 * eps)
+            fd_H[:, i] = (gp - gm) / (2 * eps)
+        scale_g = np.abs(g).max()
+        scale_H = np.abs(H).max()
+        assert np.abs(fd_g - g).max() < 1e-7 * scale_g
+        assert np.abs(fd_H - H).max() < 1e-7 * scale_H
+        assert np.abs(H - H.T).max() == 0.0
+
+
+def test_soft_grid_matches_separable_fft_evaluation():
+    """Section 2.3: the grid values of C_L0 equal the separable evaluation
+    S_mn(b_k) = sum_l c^l_mn d^l_mn(b_k) followed by a 2-D inverse DFT in (m, n)."""
+    L0, K, S, R = 4, 2, 3, 5.0
+    f, h = rand_coef(L0, S), rand_coef(L0, S)
+    c = O.correlate(f, h, S, R, L0)
+    n = O.soft_n(L0, K)
+    grid = O.soft_grid(c, L0, K).reshape(n, n, n)   # [i][k][j]
+    for k in range(n):
+        b = math.pi * (2 * k + 1) / (2 * n)
+        d = O.wigner_d(L0, b)
+        A = np.zeros((n, n), complex)
+        for l in range(L0 + 1):
+            for m in range(-l, l + 1):
+                for nn in range(-l, l + 1):
+                    i = O.c_index(l, m, nn)
+                    A[m % n, nn % n] += c[i] * d[i]
+        vals = (np.fft.ifft2(A) * n * n).real          # [i][j]
+        assert np.abs(vals - grid[:, k, :]).max() < 1e-12 * np.abs(grid).max()
+
+
+def brute_local_maxima(grid, n, P):
+    g = grid.reshape(n, n, n)
+    out = []
+    for i in range(n):
+        for k in range(n):
+            for j in range(n):
+                p = (i * n + k) * n + j
+                v = g[i, k, j]
+                ok = True
+                for di in (-1, 0, 1):
+                    for dk in (-1, 0, 1):
+                        for dj in (-1, 0, 1):
+                            if (di, dk, dj) == (0, 0, 0) or not (0 <= k + dk < n):
+                                continue
+                            q = (((i + di) % n) * n + (k + dk)) * n + (j + dj) % n
+                            w = grid[q]
+                            if not (v > w or (v == w and p < q)):
+                                ok = False
+                if ok:
+                    out.append((-v, p))
+    out.sort()
+    return [p for _, p in out[:P]]
+
+
+def test_top_p_matches_brute_force_rescan():
+    L0, K, S, R = 4, 1, 3, 5.0
+    f, h = rand_coef(L0, S), rand_coef(L0, S)
+    c = O.correlate(f, h, S, R, L0)
+    n = O.soft_n(L0, K)
+    grid = O.soft_grid(c, L0, K)
+    idx, sc = O.local_maxima_topk(grid, n, 12)
+    assert list(idx) == brute_local_maxima(grid, n, 12)
+    assert np.all(sc == grid[idx])
+    # plateaus: a constant grid has exactly one local maximum, index 0
+    idx, _ = O.local_maxima_topk(np.ones(n ** 3), n, 5)
+    assert list(idx) == [0]
+    # quantised values create ties between neighbours
+    q = np.round(grid / np.abs(grid).max() * 4) / 4
+    idx, _ = O.local_maxima_topk(q, n, 30)
+    assert list(idx) == brute_local_maxima(q, n, 30)
+
+
+def test_wrap_keeps_the_rotation():
+    for t in [(0.1, -0.2, 6.2), (7.0, 3.3, -1.0), (-0.5, 0.4, 12.0), (1.0, math.pi + 0.05, 0.3)]:
+        w = O.wrap(t)
+        assert 0 <= w[0] < 2 * math.pi and 0 <= w[1] <= math.pi and 0 <= w[2] < 2 * math.pi
+        assert np.abs(O.euler_to_matrix(*w) - O.euler_to_matrix(*t)).max() < 1e-14
+
+
+def test_newton_direction_solves_and_guards():
+    H = -np.array([[4.0, 1.0, 0.5], [1.0, 3.0, 0.2], [0.5, 0.2, 2.0]])
+    g = np.array([0.01, -0.02, 0.005])
+    d, fl = O.newton_direction(g, H, 32)
+    assert fl == 0 and np.abs(d + np.linalg.solve(H, g)).max() < 1e-16
+    # indefinite: gradient step g/||H||_F, flag bit 1
+    Hi = np.diag([-1.0, 2.0, -3.0])
+    d, fl = O.newton_direction(g, Hi, 32)
+    assert fl == 2 and np.abs(d - g / np.linalg.norm(Hi)).max() < 1e-17
+    # clamp to pi/(2(L+1))
+    d, fl = O.newton_direction(np.array([10.0, 0, 0]), H, 8)
+    assert abs(np.linalg.norm(d) - math.pi / 18) < 1e-15
+
+
+def test_newton_converges_quadratically_near_a_maximum():
+    L, S, R = 10, 3, 6.0
+    f = rand_coef(L, S)
+    h = np.zeros_like(f)
+    g_true = (1.0, 1.2, 2.0)
+    for s in range(S):
+        for l in range(L + 1):
+            hr = O.wigner_D(l, *g_true).conj().T @ full_orders(f[s], l)
+            for m in range(l + 1):
+                h[s, O.lm_index(l, m)] = hr[m + l]
+    c = O.correlate(f, h, S, R, L)     # maximum of C_L at g_true
+    t = np.array(g_true) + np.array([0.02, -0.015, 0.01])
+    norms = []
+    for _ in range(4):
+        C, gr, H, _ = O.objective(c, L, *t, derivs=True)
+        norms.append(np.linalg.norm(gr))
+        t = t - np.linalg.solve(H, gr)
+    assert norms[1] < norms[0] * 0.2 and norms[2] < norms[1] ** 2 / norms[0] * 10
+    x, sc, fl = O.newton_march(c, [L], 3, np.array(g_true) + np.array([0.02, -0.015, 0.01]))
+    assert O.rotation_angle(O.euler_to_matrix(*x), O.euler_to_matrix(*g_true)) < 1e-9
+
+
+def test_planted_rotation_recovered_on_noiseless_volumes():
+    """f = g* o h with no noise (Section 5.1's model): the exact blob rotation
+    must be recovered to discretisation accuracy, and the inverse rotation
+    must not be what comes out."""
+    w = synth.WORKLOADS["small32"]
+    d = synth.make_batch(w, exact_rotation=True, noise=False)
+    out = O.align_batch(d["particles"].numpy(), d["templates"].numpy(), S=w.n_shells, r_max=w.r_max,
+                        L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter, L_sched=w.L_sched)
+    err = O.rotation_angle(out["R"][0], d["R_true"][0])
+    assert math.degrees(err) < 0.25
+    assert O.rotation_angle(out["R"][0], d["R_true"][0].T) > 0.1
+    assert out["n_cand"][0] == w.P
