@@ -1,0 +1,199 @@
+/*
+ * matcha.h — C ABI of the GB300 (sm_103a) batched rotational-alignment library.
+ *
+ * The library computes the data-parallel path of Matcha (Kruse, Debarnot,
+ * Kishore, Dokmanic, arXiv 2603.15285): for each (particle f, template h)
+ * pair it finds g^ = argmax_g C(g), C(g) = <f, g o h>  (Section 2, Eq. maxcc_rot),
+ * by Algorithm 1: a SOFFT grid search on the bandlimited correlation C_{L0},
+ * the P strongest local maxima as candidates, and Newton steps on C_{L_j} for
+ * an increasing bandwidth schedule L_0 < L_1 < ... < L_J.
+ *
+ * Conventions shared by every entry point:
+ *   - all calls that take a `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) are asynchronous on that stream: argument
+ *     errors are returned synchronously before anything is enqueued, CUDA
+ *     launch errors are returned as MATCHA_ERR_CUDA;
+ *   - `*_dev` pointers are device memory owned by the caller; the library never
+ *     allocates or frees in those calls (only plan create/destroy do);
+ *   - precision: a plan computes either in FP64 throughout (MATCHA_FP64) or
+ *     in FP32 with FP64 angles, 3x3 solves and final comparisons (MATCHA_FP32);
+ *     "real" below is double for FP64 plans and float for FP32 plans, and a
+ *     complex number is two consecutive reals (re, im);
+ *   - volumes: float32, C order [z][y][x], N^3 per volume, voxel [k][j][i] at
+ *     position (x, y, z) = (i, j, k), rotation centre c0 = N/2, trilinear
+ *     interpolation with zero outside the box;
+ *   - Euler angles: ZYZ radians, g = r_z(alpha) r_y(beta) r_z(gamma)
+ *     (Appendix A.3, Eq. Euler), alpha, gamma in [0, 2pi), beta in [0, pi];
+ *     rotation matrices are row-major 3x3 doubles.
+ *
+ * Layouts:
+ *   SH coefficients (matcha_analyze):  [b][s][lm] complex, lm = l(l+1)/2 + m,
+ *     0 <= m <= l <= L_J, s < n_shells.  Negative orders of these real volumes
+ *     follow from f_{l,-m} = (-1)^m conj(f_{lm}).
+ *   correlation coefficients (matcha_correlate_coeffs): per particle,
+ *     for each order pair (m, n) with 0 <= m <= L_J and -m <= n <= m (pair
+ *     index q = m*m + n + m, pairs in increasing q), for l = m .. L_J, the two
+ *     complex numbers (c^l_{mn}, c^l_{nm}).  Entry (q, l) starts at complex
+ *     index 2 * (off(m, n) + l - m) with
+ *     off(m, n) = sum_{m' < m} (2m'+1)(L_J-m'+1) + (n+m)(L_J-m+1);
+ *     matcha_plan_info() returns the entry count.  These pairs and their
+ *     images under c^l_{-m,-n} = (-1)^{m+n} conj(c^l_{mn}) give every
+ *     coefficient with |m|, |n| <= l <= L_J.
+ *   SOFFT grid (workspace): n = 2K(L0+1) points per angle, alpha_i = 2 pi i/n,
+ *     beta_k = pi (2k+1)/(2n), gamma_j = 2 pi j/n, linear index (i n + k) n + j.
+ */
+#ifndef MATCHA_H
+#define MATCHA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MATCHA_MAX_LEVELS 16
+#define MATCHA_MAX_L 64
+#define MATCHA_MAX_P 32
+
+typedef struct matcha_plan_s *matcha_plan;
+
+typedef enum {
+  MATCHA_OK = 0,
+  MATCHA_ERR_INVALID_ARG = 1, /* bad pointer, size or descriptor field */
+  MATCHA_ERR_CUDA = 2,        /* a CUDA call or kernel launch failed */
+  MATCHA_ERR_WORKSPACE = 3,   /* workspace smaller than matcha_workspace_size */
+  MATCHA_ERR_TIMEOUT = 4,     /* reserved for bounded device-side waits */
+  MATCHA_ERR_UNSUPPORTED = 5  /* valid but not implemented (e.g. a size limit) */
+} matcha_status;
+
+typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1 } matcha_precision;
+
+/* Plan descriptor: the parameters of Algorithm 1 plus the sampling of the ball.
+ *   box_n        N, volume edge (4 .. 512)
+ *   n_shells     S, Gauss-Legendre radial shells on (0, r_max] (1 .. 128)
+ *   r_max        outer shell radius in voxels; <= 0 selects N/2 - 1
+ *   L0           SOFFT bandwidth (Section 2.3), 1 .. 32, equal to L_sched[0]
+ *   K_oversample SOFFT oversampling K (1 .. 4)
+ *   P_max        candidates kept per particle, 1 .. MATCHA_MAX_P
+ *   M_iter       Newton steps per level, 1 .. 32
+ *   n_levels     number of bandwidth levels J+1 (L_sched[0] = L0 is the
+ *                optional refinement on C_{L0}), 1 .. MATCHA_MAX_LEVELS
+ *   L_sched      strictly increasing bandwidths, last = L_J <= MATCHA_MAX_L
+ *   precision    matcha_precision
+ *   step_tol     Newton early stop (Section 2.4): a level stops for a candidate
+ *                once ||delta||_2 < step_tol (radians); <= 0 selects 1e-9 for
+ *                FP64 plans and 1e-6 for FP32 plans.
+ * The angular sampling is n_theta = L_J + 1 Gauss-Legendre nodes in cos(theta)
+ * and n_phi = 2 L_J + 2 equispaced phi per shell. */
+typedef struct {
+  int box_n;
+  int n_shells;
+  double r_max;
+  int L0;
+  int K_oversample;
+  int P_max;
+  int M_iter;
+  int n_levels;
+  int L_sched[MATCHA_MAX_LEVELS];
+  int precision;
+  double step_tol;
+} matcha_plan_desc;
+
+/* Sizes derived from a plan. */
+typedef struct {
+  int n_lm;            /* (L_J+1)(L_J+2)/2 SH coefficients per shell */
+  long coeff_count;    /* complex SH coefficients per volume = n_shells * n_lm */
+  long corr_entries;   /* (pair, l) entries per particle; 2 complex each */
+  int n_pairs;         /* (L_J+1)^2 order pairs */
+  int soft_n;          /* SOFFT points per angle, 2K(L0+1) */
+  int real_bytes;      /* 8 (FP64) or 4 (FP32) */
+} matcha_plan_info_t;
+
+/* Builds the quadrature, Legendre, twiddle, Wigner-recurrence and SOFFT
+ * tables of the plan on the current CUDA device (Appendix A.1-A.5 supply the
+ * definitions) and synchronises.  *out receives the plan (NULL on error).
+ * Allocates device memory owned by the plan. */
+matcha_status matcha_plan_create(const matcha_plan_desc *desc, matcha_plan *out);
+/* Frees the plan's tables; NULL is accepted. Synchronises the device. */
+matcha_status matcha_plan_destroy(matcha_plan plan);
+matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info);
+
+/* Device table access for tests: which = 0 radial nodes r_s, 1 radial weights
+ * w_s (r^2 included), 2 angular nodes cos(theta_j), 3 angular weights; all
+ * doubles.  *dev receives a device pointer owned by the plan, *count its
+ * length. */
+matcha_status matcha_plan_table(matcha_plan plan, int which, const void **dev, long *count);
+
+/* Workspace bytes matcha_align needs for B particles. */
+matcha_status matcha_workspace_size(matcha_plan plan, int B, size_t *bytes);
+
+/* a1+a2: shell sampling and SH analysis (Appendix A.1 with radial shells in
+ * place of the radial Bessel basis).  vols_dev: B float32 volumes; coeffs_dev:
+ * B * coeff_count complex reals, layout above. */
+matcha_status matcha_analyze(matcha_plan plan, const float *vols_dev, int B, void *coeffs_dev,
+                             void *stream);
+
+/* a3: per-degree contraction, Eq. (sigmalmm):
+ *   c^l_{mn} = sum_s w_s f_lm(r_s) conj(h_ln(r_s)).
+ * f_dev: B particles' SH coefficients; h_dev: templates' coefficients, with
+ * template index b * h_batch_stride (0 = one shared template, 1 = one per
+ * particle).  c_dev: B * corr_entries * 2 complex reals. */
+matcha_status matcha_correlate_coeffs(matcha_plan plan, const void *f_dev, const void *h_dev,
+                                      int B, int h_batch_stride, void *c_dev, void *stream);
+
+/* a4+a5: C_{L0} on the SOFFT grid (Section 2.3, beta transform plus 2-D DFT)
+ * and the P strongest local maxima.  P_per_dev (nullable) gives a per-particle
+ * P_b <= P_max.  Outputs, [B][P_max] each: idx_dev (linear grid index, -1
+ * past n_cand), euler_dev ([B][P_max][3] grid angles), score_dev (grid value);
+ * n_cand_dev [B].  grid_dev: B * soft_n^3 reals of scratch. */
+matcha_status matcha_soft_search(matcha_plan plan, const void *c_dev, int B, const int *P_per_dev,
+                                 void *grid_dev, int *idx_dev, double *euler_dev,
+                                 double *score_dev, int *n_cand_dev, void *stream);
+
+/* a6: frequency-marched Newton refinement of every candidate (Sections
+ * 2.2-2.4, Algorithm 1).  euler_dev is read as the start points and
+ * overwritten by the refined angles; score_dev receives C_{L_J} at the
+ * refined angles; cand_flags_dev [B][P_max] receives bit 0 non-finite value,
+ * bit 1 gradient fallback (-H not positive definite), bit 2 a step with no
+ * accepted trial. */
+matcha_status matcha_newton_march(matcha_plan plan, const void *c_dev, int B,
+                                  const int *n_cand_dev, double *euler_dev, double *score_dev,
+                                  int *cand_flags_dev, void *stream);
+
+/* a7: argmax_p C_{L_J} (ties to the smaller p, NaN skipped), Euler -> matrix.
+ * flags_dev [B]: OR of the candidates' flags, plus bit 3 when fewer than P_b
+ * local maxima existed. */
+matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per_dev,
+                                  const int *n_cand_dev, const double *cand_euler_dev,
+                                  const double *cand_score_dev, const int *cand_flags_dev,
+                                  double *euler_dev, double *R_dev, double *score_dev,
+                                  int *best_p_dev, int *flags_dev, void *stream);
+
+/* The whole path (a1..a7) for B pairs: particles_dev B volumes, templates_dev
+ * volume b * template_batch_stride (0 or 1).  Outputs euler [B][3], R [B][9],
+ * score [B], best_p [B], flags [B].  ws_dev must hold
+ * matcha_workspace_size(plan, B) bytes (256-byte aligned). */
+matcha_status matcha_align(matcha_plan plan, const float *particles_dev, const float *templates_dev,
+                           int B, int template_batch_stride, const int *P_per_dev,
+                           double *euler_dev, double *R_dev, double *score_dev, int *best_p_dev,
+                           int *flags_dev, void *ws_dev, size_t ws_bytes, void *stream);
+
+/* matcha_align on HOST buffers: copies the volumes to the device (into the
+ * workspace, which must hold matcha_host_workspace_size bytes), runs the
+ * path, copies the results back and synchronises the stream.  Host buffers
+ * may be pageable; pinned buffers give full copy bandwidth. */
+matcha_status matcha_host_workspace_size(matcha_plan plan, int B, int template_batch_stride,
+                                         size_t *bytes);
+matcha_status matcha_align_host(matcha_plan plan, const float *particles, const float *templates,
+                                int B, int template_batch_stride, double *euler, double *R,
+                                double *score, int *best_p, int *flags, void *ws_dev,
+                                size_t ws_bytes, void *stream);
+
+const char *matcha_status_string(matcha_status s);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *matcha_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MATCHA_H */

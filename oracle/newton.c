@@ -14,7 +14,9 @@
  *   4. trial theta' = wrap(theta + delta); accept when C_{L_j}(theta') >=
  *      C_{L_j}(theta), else halve delta, at most twice; when no trial is
  *      accepted theta stays (flag bit 2);
- *   5. exactly M_iter steps per level, no early stop;
+ *   5. at most M_iter steps per level; the level ends early for a candidate
+ *      once ||delta||_2 (after step 2) is below step_tol, the "parameter
+ *      increment below a prescribed tolerance" stop of Section 2.4;
  *   a non-finite C, grad or H stops the march (flag bit 0).
  * wrap: alpha, gamma mod 2 pi; beta < 0 -> (a+pi, -b, g+pi); beta > pi ->
  * (a+pi, 2pi-b, g+pi), since r_z(pi) r_y(b) r_z(pi) = r_y(-b).
@@ -90,7 +92,7 @@ static int finite_all(double C, const double *g, const double *H) {
 /* Refines abg in place through the schedule; *score = C_{L_J}(abg).
  * Returns flag bits. */
 int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_iter,
-                     double *abg, double *score) {
+                     double step_tol, double *abg, double *score) {
   int flags = 0;
   double C = NAN;
   for (int lev = 0; lev < n_levels; ++lev) {
@@ -100,6 +102,7 @@ int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_it
       C = orc_objective(c, L, abg[0], abg[1], abg[2], g, H, NULL);
       if (!finite_all(C, g, H)) { *score = C; return flags | 1; }
       flags |= orc_newton_direction(g, H, L, delta);
+      if (sqrt(delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2]) < step_tol) break;
       int accepted = 0;
       for (int h = 0; h < 3 && !accepted; ++h) {
         double trial[3] = {abg[0] + delta[0], abg[1] + delta[1], abg[2] + delta[2]};
