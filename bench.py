@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of batched Matcha rotational alignment on GB300.
+
+Workload: 1024 (particle, template) pairs of 64^3 Gaussian-blob volumes
+(48 blobs, sigma 2, SNR 0.1, +-60 degree missing wedge), 32 shells, SOFFT at
+L0 = 8 with K = 2 and the top 16 candidates, Newton levels 8 -> 16 -> 24 -> 32
+with 3 steps each.  A step is one pass of the whole path (shell sampling + SH
+analysis of both volumes, contraction, SOFFT grid, top-P, Newton march, final
+argmax) over the batch, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl matcha|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank aligns its own 1024
+particles (weak scaling, no data-path collective).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles aligned/sec at 64^3, final L=32 (ang. err ≤0.05° vs FP64 oracle)"
+UNIT = "particles/s"
+WORKLOAD = "batch64"
+# FP32 ops per Wigner recurrence step, counted from the Newton kernel source
+# (an FMA counts 2): derivative evaluation 20 (d, d', d'' recurrence) + 24
+# (12 FMA accumulations); value-only evaluation 5 + 8.
+FLOPS_FULL_STEP = 44
+FLOPS_VALUE_STEP = 13
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="matcha", choices=["matcha", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(w, B, ws):
+    return {
+        "workload": "%s: %d (particle, template) pairs of %d^3 float32 Gaussian-blob volumes per GPU "
+                    "(%d blobs, sigma %.1f, SNR %.2f, wedge +-%d deg), %d shells, SOFFT L0=%d K=%d "
+                    "top-%d, Newton L=%s x%d" % (w.name, B, w.N, w.n_blobs, w.sigma, w.snr,
+                                                  int(w.wedge_deg), w.n_shells, w.L0, w.K, w.P,
+                                                  "->".join(map(str, w.L_sched)), w.M_iter),
+        "particles_per_gpu": B, "box": w.N, "shells": w.n_shells, "L_final": w.L_final,
+        "L0": w.L0, "K": w.K, "P": w.P, "M_iter": w.M_iter,
+        "parallelism": "dp%d (particles sharded, no collective)" % ws,
+        "l2": "inputs %.1f GiB per step > 129 MB L2; no flush" % (2 * B * w.N ** 3 * 4 / 2 ** 30),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """The oracle (FP64 C, all host cores) on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    w = synth.WORKLOADS[WORKLOAD]
+    cores = oracle.max_threads()
+    n = max(1, cores)
+    d = synth.make_batch(w, B=n)
+    parts, temps = d["particles"].numpy(), d["templates"].numpy()
+    kw = dict(S=w.n_shells, r_max=w.r_max, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter, L_sched=w.L_sched)
+    for _ in range(args.warmup):
+        oracle.align_batch(parts[:1], temps[:1], **kw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.align_batch(parts, temps, **kw)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = n / dt
+    sample = "%d particles of %s per step (one per host thread), FP64 C oracle" % (n, WORKLOAD)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, n, 1),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_15285_gb300 as m
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    B = args.batch or w.B
+    d = synth.make_batch(w, B=B, start=rank * B, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    prec = m.FP32 if args.precision == "fp32" else m.FP64
+    plan = m.plan_for_workload(w, precision=prec)
+    n = plan.info.soft_n
+    rt = plan.real_dtype
+    f = torch.empty((B, w.n_shells, plan.info.n_lm, 2), dtype=rt, device="cuda")
+    h = torch.empty_like(f)
+    c = torch.empty((B, plan.info.corr_entries, 2, 2), dtype=rt, device="cuda")
+    grid = torch.empty((B, n, n, n), dtype=rt, device="cuda")
+    work = torch.zeros((B, 2), dtype=torch.int64, device="cuda")
+    L = m.lib()
+    st = torch.cuda.current_stream()
+    sp = st.cuda_stream
+    idx = torch.empty((B, w.P), dtype=torch.int32, device="cuda")
+    ceu = torch.empty((B, w.P, 3), dtype=torch.float64, device="cuda")
+    csc = torch.empty((B, w.P), dtype=torch.float64, device="cuda")
+    cfl = torch.empty((B, w.P), dtype=torch.int32, device="cuda")
+    ncd = torch.empty((B,), dtype=torch.int32, device="cuda")
+    out = dict(euler=torch.empty((B, 3), dtype=torch.float64, device="cuda"),
+               R=torch.empty((B, 3, 3), dtype=torch.float64, device="cuda"),
+               score=torch.empty((B,), dtype=torch.float64, device="cuda"),
+               best_p=torch.empty((B,), dtype=torch.int32, device="cuda"),
+               flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
+    H = plan.handle
+    stages = ["analyze", "correlate", "soft", "newton", "select"]
+    KERNELS_PER_STEP = 7  # analyze x2, correlate, soft grid, top-P, newton, final select
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(st)
+        mark(0)
+        m._check(L.matcha_analyze(H, parts.data_ptr(), B, f.data_ptr(), sp), "analyze")
+        m._check(L.matcha_analyze(H, temps.data_ptr(), temps.shape[0], h.data_ptr(), sp), "analyze")
+        mark(1)
+        m._check(L.matcha_correlate_coeffs(H, f.data_ptr(), h.data_ptr(), B,
+                                           1 if temps.shape[0] == B else 0, c.data_ptr(), sp), "corr")
+        mark(2)
+        m._check(L.matcha_soft_search(H, c.data_ptr(), B, None, grid.data_ptr(), idx.data_ptr(),
+                                      ceu.data_ptr(), csc.data_ptr(), ncd.data_ptr(), sp), "soft")
+        mark(3)
+        m._check(L.matcha_newton_march(H, c.data_ptr(), B, ncd.data_ptr(), ceu.data_ptr(),
+                                       csc.data_ptr(), cfl.data_ptr(), work.data_ptr(), sp), "newton")
+        mark(4)
+        m._check(L.matcha_final_select(H, B, None, ncd.data_ptr(), ceu.data_ptr(), csc.data_ptr(),
+                                       cfl.data_ptr(), out["euler"].data_ptr(), out["R"].data_ptr(),
+                                       out["score"].data_ptr(), out["best_p"].data_ptr(),
+                                       out["flags"].data_ptr(), sp), "select")
+        mark(5)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(st)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    stage_ms = {s: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                for i, s in enumerate(stages)}
+    wk = work.sum(0).cpu().numpy()
+    newton_flops = FLOPS_FULL_STEP * float(wk[0]) + FLOPS_VALUE_STEP * float(wk[1])
+    clk = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12  # TFLOP/s
+    fp64_peak = SMS * 2 * 2 * clk * 1e6 / 1e12
+    achieved = newton_flops / (stage_ms["newton"] * 1e-3) / 1e12
+    peak = fp32_peak if prec == m.FP32 else fp64_peak
+    value = ws * B / (ms * 1e-3)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == m.FP32 else "f64",
+        "data": "synthetic (seeded Gaussian-blob volumes; no dataset)",
+        "config": workload_config(w, B, ws),
+        "stage_ms": stage_ms,
+        "roofline": {"kernel": "k_newton", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "%d SMs x %d %s lanes x 2 x %.0f MHz (max SM clock seen)"
+                                    % (SMS, FP32_LANES if prec == m.FP32 else 2,
+                                       "FP32" if prec == m.FP32 else "FP64", clk),
+                     "flops_per_launch": newton_flops},
+        "clocks": clocks,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+    }
+    # accuracy of the timed path against the FP64 GPU path (oracle-checked in the tests)
+    if rank == 0 and not args.no_fp64 and prec == m.FP32:
+        plan64 = m.plan_for_workload(w, precision=m.FP64)
+        ws64 = m.alloc_workspace(plan64, B)
+        o64 = m.matcha_align(plan64, parts, temps, ws=ws64)
+        torch.cuda.synchronize()
+        k64 = max(2, args.steps // 25)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k64):
+            m.matcha_align(plan64, parts, temps, ws=ws64, out=o64)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        import oracle
+        R32, R64 = out["R"].cpu().numpy(), o64["R"].cpu().numpy()
+        errs = np.degrees([oracle.rotation_angle(R32[b], R64[b]) for b in range(B)])
+        res["fp64_path"] = {"value": B / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                            "steps": k64}
+        res["accuracy"] = {"max_err_deg_vs_fp64_gpu": float(errs.max()),
+                           "p90_err_deg_vs_fp64_gpu": float(np.percentile(errs, 90)),
+                           "particles_over_0.05deg": int((errs > 0.05).sum()),
+                           "note": "FP64 GPU path matches the FP64 oracle to 1e-8 rad (tests)"}
+        del ws64
+    if not args.no_e2e:
+        hp = torch.empty_like(parts, device="cpu").pin_memory()
+        hp.copy_(parts)
+        ht = torch.empty_like(temps, device="cpu").pin_memory()
+        ht.copy_(temps)
+        stride = 1 if temps.shape[0] == B else 0
+        hws = torch.empty((plan.host_workspace_size(B, stride) + 256,), dtype=torch.uint8, device="cuda")
+        hout = dict(euler=torch.empty((B, 3), dtype=torch.float64).pin_memory(),
+                    R=torch.empty((B, 3, 3), dtype=torch.float64).pin_memory(),
+                    score=torch.empty((B,), dtype=torch.float64).pin_memory(),
+                    best_p=torch.empty((B,), dtype=torch.int32).pin_memory(),
+                    flags=torch.empty((B,), dtype=torch.int32).pin_memory())
+        m.matcha_align_host(plan, hp, ht, ws=hws, out=hout)
+        ke = max(3, args.steps // 10)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            m.matcha_align_host(plan, hp, ht, ws=hws, out=hout)
+        te = (time.perf_counter() - t0) / ke
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        res["e2e"] = {"value": ws * B / te, "unit": UNIT,
+                      "h2d_bytes_per_step": int(hp.numel() * 4 + ht.numel() * 4),
+                      "d2h_bytes_per_step": int(B * (13 * 8 + 2 * 4)),
+                      "api": "matcha_align_host (pinned host buffers, copies inside the call)"}
+        del hws
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.max_threads()
+        nb = min(B, 2 * cores)
+        kw = dict(S=w.n_shells, r_max=w.r_max, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter,
+                  L_sched=w.L_sched)
+        pc, tc = parts[:nb].cpu().numpy(), temps[:nb].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.align_batch(pc, tc, **kw)
+        tcpu = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": nb / tcpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "first %d particles of the batch, FP64 C oracle, %.1f s"
+                                         % (nb, tcpu)}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

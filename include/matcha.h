@@ -118,11 +118,13 @@ matcha_status matcha_plan_create(const matcha_plan_desc *desc, matcha_plan *out)
 matcha_status matcha_plan_destroy(matcha_plan plan);
 matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info);
 
-/* Device table access for tests: which = 0 radial nodes r_s, 1 radial weights
- * w_s (r^2 included), 2 angular nodes cos(theta_j), 3 angular weights; all
- * doubles.  *dev receives a device pointer owned by the plan, *count its
- * length. */
-matcha_status matcha_plan_table(matcha_plan plan, int which, const void **dev, long *count);
+/* Copies one of the plan's FP64 quadrature tables to the host (synchronous):
+ * which = 0 radial nodes r_s, 1 radial weights w_s (r^2 Jacobian included),
+ * 2 angular nodes cos(theta_j), 3 angular weights w_j.  *count receives the
+ * table length; at most `capacity` values are written to host_out (which may
+ * be NULL to query the length). */
+matcha_status matcha_plan_table(matcha_plan plan, int which, double *host_out, long capacity,
+                                long *count);
 
 /* Workspace bytes matcha_align needs for B particles. */
 matcha_status matcha_workspace_size(matcha_plan plan, int B, size_t *bytes);
@@ -155,10 +157,13 @@ matcha_status matcha_soft_search(matcha_plan plan, const void *c_dev, int B, con
  * overwritten by the refined angles; score_dev receives C_{L_J} at the
  * refined angles; cand_flags_dev [B][P_max] receives bit 0 non-finite value,
  * bit 1 gradient fallback (-H not positive definite), bit 2 a step with no
- * accepted trial. */
+ * accepted trial.  work_dev (nullable) [B][2] receives, per particle, the
+ * number of Wigner recurrence steps (one order pair, one degree, one
+ * candidate) taken by evaluations with derivatives and by value-only trial
+ * evaluations; it measures the work the march performed. */
 matcha_status matcha_newton_march(matcha_plan plan, const void *c_dev, int B,
                                   const int *n_cand_dev, double *euler_dev, double *score_dev,
-                                  int *cand_flags_dev, void *stream);
+                                  int *cand_flags_dev, long long *work_dev, void *stream);
 
 /* a7: argmax_p C_{L_J} (ties to the smaller p, NaN skipped), Euler -> matrix.
  * flags_dev [B]: OR of the candidates' flags, plus bit 3 when fewer than P_b

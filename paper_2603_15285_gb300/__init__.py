@@ -1,0 +1,331 @@
+"""Python binding of the matcha C ABI (``include/matcha.h``).
+
+Argument marshalling only: every step of the alignment path runs in the CUDA
+kernels of ``_lib/libmatcha.so``.  Device buffers are torch tensors (used for
+memory and streams); calls are enqueued on torch's current CUDA stream.
+There is no CPU fallback: without the compiled library or a GPU the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmatcha.so")
+
+MATCHA_MAX_LEVELS = 16
+MATCHA_MAX_L = 64
+MATCHA_MAX_P = 32
+FP64, FP32 = 0, 1
+
+# exported symbols, in include/matcha.h order
+SYMBOLS = [
+    "matcha_plan_create", "matcha_plan_destroy", "matcha_plan_info", "matcha_plan_table",
+    "matcha_workspace_size", "matcha_analyze", "matcha_correlate_coeffs", "matcha_soft_search",
+    "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
+    "matcha_align_host", "matcha_status_string", "matcha_last_error",
+]
+
+
+class MatchaError(RuntimeError):
+    pass
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("box_n", ctypes.c_int), ("n_shells", ctypes.c_int), ("r_max", ctypes.c_double),
+                ("L0", ctypes.c_int), ("K_oversample", ctypes.c_int), ("P_max", ctypes.c_int),
+                ("M_iter", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("L_sched", ctypes.c_int * MATCHA_MAX_LEVELS), ("precision", ctypes.c_int),
+                ("step_tol", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_lm", ctypes.c_int), ("coeff_count", ctypes.c_long),
+                ("corr_entries", ctypes.c_long), ("n_pairs", ctypes.c_int),
+                ("soft_n", ctypes.c_int), ("real_bytes", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MatchaError("libmatcha.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        i, l, d, sz = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_size_t
+        sigs = {
+            "matcha_plan_create": [ctypes.POINTER(PlanDesc), ctypes.POINTER(_vp)],
+            "matcha_plan_destroy": [_vp],
+            "matcha_plan_info": [_vp, ctypes.POINTER(PlanInfo)],
+            "matcha_plan_table": [_vp, i, _vp, l, ctypes.POINTER(l)],
+            "matcha_workspace_size": [_vp, i, ctypes.POINTER(sz)],
+            "matcha_analyze": [_vp, _vp, i, _vp, _vp],
+            "matcha_correlate_coeffs": [_vp, _vp, _vp, i, i, _vp, _vp],
+            "matcha_soft_search": [_vp, _vp, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+            "matcha_newton_march": [_vp, _vp, i, _vp, _vp, _vp, _vp, _vp, _vp],
+            "matcha_final_select": [_vp, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+            "matcha_align": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
+            "matcha_host_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
+            "matcha_align_host": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.matcha_status_string.argtypes = [ctypes.c_int]
+        L.matcha_status_string.restype = ctypes.c_char_p
+        L.matcha_last_error.argtypes = []
+        L.matcha_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = lib()
+        raise MatchaError("%s: %s (%s)" % (what, L.matcha_status_string(status).decode(),
+                                           L.matcha_last_error().decode()))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise MatchaError("matcha needs a CUDA device; no CPU path exists")
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Plan:
+    """A plan: Algorithm 1's parameters plus the device tables (step a0)."""
+
+    def __init__(self, box_n: int, n_shells: int, L0: int, K: int, P: int, M_iter: int,
+                 L_sched: Sequence[int], precision: int = FP64, r_max: float = 0.0,
+                 step_tol: float = 0.0):
+        _torch()
+        d = PlanDesc()
+        d.box_n, d.n_shells, d.r_max = box_n, n_shells, r_max
+        d.L0, d.K_oversample, d.P_max, d.M_iter = L0, K, P, M_iter
+        d.n_levels = len(L_sched)
+        if not 1 <= len(L_sched) <= MATCHA_MAX_LEVELS:
+            raise MatchaError("matcha_plan_create: invalid argument (L_sched length)")
+        for k, L in enumerate(L_sched):
+            d.L_sched[k] = int(L)
+        d.precision, d.step_tol = precision, step_tol
+        h = _vp()
+        _check(lib().matcha_plan_create(ctypes.byref(d), ctypes.byref(h)), "matcha_plan_create")
+        self._h = h
+        self.desc = d
+        info = PlanInfo()
+        _check(lib().matcha_plan_info(h, ctypes.byref(info)), "matcha_plan_info")
+        self.info = info
+        self.precision = precision
+        self.P = P
+        self.L_final = int(L_sched[-1])
+        self.box_n = box_n
+        self.n_shells = n_shells
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def real_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.precision == FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().matcha_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def table(self, which: int) -> np.ndarray:
+        n = ctypes.c_long()
+        _check(lib().matcha_plan_table(self._h, which, None, 0, ctypes.byref(n)), "matcha_plan_table")
+        out = np.zeros(n.value)
+        _check(lib().matcha_plan_table(self._h, which, out.ctypes.data, n.value, ctypes.byref(n)),
+               "matcha_plan_table")
+        return out
+
+    def workspace_size(self, B: int) -> int:
+        s = ctypes.c_size_t()
+        _check(lib().matcha_workspace_size(self._h, B, ctypes.byref(s)), "matcha_workspace_size")
+        return s.value
+
+    def host_workspace_size(self, B: int, template_batch_stride: int) -> int:
+        s = ctypes.c_size_t()
+        _check(lib().matcha_host_workspace_size(self._h, B, template_batch_stride, ctypes.byref(s)),
+               "matcha_host_workspace_size")
+        return s.value
+
+
+def _need(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise MatchaError("%s must be a contiguous CUDA tensor of %s" % (name, dtype))
+
+
+def matcha_analyze(plan: Plan, vols):
+    torch = _torch()
+    _need(vols, torch.float32, "vols")
+    B = vols.shape[0]
+    out = torch.empty((B, plan.n_shells, plan.info.n_lm, 2), dtype=plan.real_dtype, device="cuda")
+    _check(lib().matcha_analyze(plan.handle, _ptr(vols), B, _ptr(out), _stream()), "matcha_analyze")
+    return out
+
+
+def matcha_correlate_coeffs(plan: Plan, f, h, h_batch_stride: int):
+    torch = _torch()
+    _need(f, plan.real_dtype, "f"); _need(h, plan.real_dtype, "h")
+    B = f.shape[0]
+    c = torch.empty((B, plan.info.corr_entries, 2, 2), dtype=plan.real_dtype, device="cuda")
+    _check(lib().matcha_correlate_coeffs(plan.handle, _ptr(f), _ptr(h), B, h_batch_stride, _ptr(c),
+                                         _stream()), "matcha_correlate_coeffs")
+    return c
+
+
+def matcha_soft_search(plan: Plan, c, P_per=None, grid=None):
+    torch = _torch()
+    _need(c, plan.real_dtype, "c")
+    B = c.shape[0]
+    n = plan.info.soft_n
+    if grid is None:
+        grid = torch.empty((B, n, n, n), dtype=plan.real_dtype, device="cuda")
+    P = plan.P
+    idx = torch.empty((B, P), dtype=torch.int32, device="cuda")
+    euler = torch.empty((B, P, 3), dtype=torch.float64, device="cuda")
+    score = torch.empty((B, P), dtype=torch.float64, device="cuda")
+    ncand = torch.empty((B,), dtype=torch.int32, device="cuda")
+    if P_per is not None:
+        _need(P_per, torch.int32, "P_per")
+    _check(lib().matcha_soft_search(plan.handle, _ptr(c), B, _ptr(P_per), _ptr(grid), _ptr(idx),
+                                    _ptr(euler), _ptr(score), _ptr(ncand), _stream()),
+           "matcha_soft_search")
+    return dict(grid=grid, idx=idx, euler=euler, score=score, n_cand=ncand)
+
+
+def matcha_newton_march(plan: Plan, c, n_cand, euler, work=None, score=None, flags=None):
+    """Refines ``euler`` in place; ``work`` (optional int64 [B][2]) receives
+    the recurrence-step counts of derivative and value-only evaluations."""
+    torch = _torch()
+    _need(c, plan.real_dtype, "c"); _need(n_cand, torch.int32, "n_cand")
+    _need(euler, torch.float64, "euler")
+    B = c.shape[0]
+    if score is None:
+        score = torch.full((B, plan.P), float("nan"), dtype=torch.float64, device="cuda")
+    if flags is None:
+        flags = torch.zeros((B, plan.P), dtype=torch.int32, device="cuda")
+    if work is not None:
+        _need(work, torch.int64, "work")
+    _check(lib().matcha_newton_march(plan.handle, _ptr(c), B, _ptr(n_cand), _ptr(euler), _ptr(score),
+                                     _ptr(flags), _ptr(work), _stream()), "matcha_newton_march")
+    return dict(euler=euler, score=score, flags=flags, work=work)
+
+
+def matcha_final_select(plan: Plan, n_cand, cand_euler, cand_score, cand_flags, P_per=None):
+    torch = _torch()
+    B = n_cand.shape[0]
+    euler = torch.empty((B, 3), dtype=torch.float64, device="cuda")
+    R = torch.empty((B, 3, 3), dtype=torch.float64, device="cuda")
+    score = torch.empty((B,), dtype=torch.float64, device="cuda")
+    best = torch.empty((B,), dtype=torch.int32, device="cuda")
+    flags = torch.empty((B,), dtype=torch.int32, device="cuda")
+    _check(lib().matcha_final_select(plan.handle, B, _ptr(P_per), _ptr(n_cand), _ptr(cand_euler),
+                                     _ptr(cand_score), _ptr(cand_flags), _ptr(euler), _ptr(R),
+                                     _ptr(score), _ptr(best), _ptr(flags), _stream()),
+           "matcha_final_select")
+    return dict(euler=euler, R=R, score=score, best_p=best, flags=flags)
+
+
+def alloc_workspace(plan: Plan, B: int):
+    torch = _torch()
+    nbytes = plan.workspace_size(B)
+    return torch.empty((nbytes + 256,), dtype=torch.uint8, device="cuda")
+
+
+def matcha_align(plan: Plan, particles, templates, P_per=None, ws=None, out=None):
+    """The whole path on device tensors; ``templates`` holds B volumes or one shared."""
+    torch = _torch()
+    _need(particles, torch.float32, "particles"); _need(templates, torch.float32, "templates")
+    B = particles.shape[0]
+    stride = 0 if templates.shape[0] == 1 and B != 1 else 1
+    if ws is None:
+        ws = alloc_workspace(plan, B)
+    if out is None:
+        out = dict(euler=torch.empty((B, 3), dtype=torch.float64, device="cuda"),
+                   R=torch.empty((B, 3, 3), dtype=torch.float64, device="cuda"),
+                   score=torch.empty((B,), dtype=torch.float64, device="cuda"),
+                   best_p=torch.empty((B,), dtype=torch.int32, device="cuda"),
+                   flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    nbytes = ws.numel() - (aligned - base)
+    _check(lib().matcha_align(plan.handle, _ptr(particles), _ptr(templates), B, stride, _ptr(P_per),
+                              _ptr(out["euler"]), _ptr(out["R"]), _ptr(out["score"]),
+                              _ptr(out["best_p"]), _ptr(out["flags"]), aligned, nbytes, _stream()),
+           "matcha_align")
+    return out
+
+
+def matcha_align_host(plan: Plan, particles: np.ndarray, templates: np.ndarray, ws=None,
+                      out=None):
+    """matcha_align on host arrays (float32, [B][N][N][N]); copies are inside the call."""
+    torch = _torch()
+    B = particles.shape[0]
+    stride = 0 if templates.shape[0] == 1 and B != 1 else 1
+    if ws is None:
+        ws = torch.empty((plan.host_workspace_size(B, stride) + 256,), dtype=torch.uint8,
+                         device="cuda")
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    nbytes = ws.numel() - (aligned - base)
+    if out is None:
+        out = dict(euler=np.empty((B, 3)), R=np.empty((B, 3, 3)), score=np.empty(B),
+                   best_p=np.empty(B, dtype=np.int32), flags=np.empty(B, dtype=np.int32))
+
+    def hp(a):
+        if isinstance(a, torch.Tensor):
+            return a.data_ptr()
+        return a.ctypes.data
+    _check(lib().matcha_align_host(plan.handle, hp(particles), hp(templates), B, stride,
+                                   hp(out["euler"]), hp(out["R"]), hp(out["score"]),
+                                   hp(out["best_p"]), hp(out["flags"]), aligned, nbytes, _stream()),
+           "matcha_align_host")
+    return out
+
+
+def corr_layout(L: int):
+    """(m, n, l) of every correlation entry in the library's pair layout."""
+    rows = []
+    for m in range(L + 1):
+        for n in range(-m, m + 1):
+            for l in range(m, L + 1):
+                rows.append((m, n, l))
+    return np.array(rows, dtype=np.int64)
+
+
+def plan_for_workload(w, precision: int = FP64, **kw) -> Plan:
+    """A plan with the parameters of a ``synth.Workload``."""
+    return Plan(box_n=w.N, n_shells=w.n_shells, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter,
+                L_sched=w.L_sched, precision=precision, r_max=w.r_max, **kw)

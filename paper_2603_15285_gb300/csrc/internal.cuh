@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (see include/matcha.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../../include/matcha.h"
+
+namespace matcha {
+
+// Plan: descriptor, derived sizes and the device tables it owns.
+struct Plan {
+  matcha_plan_desc desc;
+  int N, S, LJ, L0, K, P, M, nlev;
+  int Ls[MATCHA_MAX_LEVELS];
+  double R, step_tol;
+  bool fp64;
+  int nt, np, nlm, npairs, npairs0, ns;
+  long nc;   // (pair, l) entries per particle, l <= L_J
+  long nc0;  // (pair, l) entries with m <= L0 and l <= L0 (SOFFT layout)
+  // device tables (one allocation)
+  void *base = nullptr;
+  double *rs, *wrad, *xj, *wj;  // S, S, nt, nt (FP64 always)
+  void *ptab;                   // real [nlm][nt]: w_j (2 pi / n_phi) Pbar_lm(x_j)
+  void *phi_cs;                 // real [np][2]: cos, sin (2 pi k / n_phi)
+  void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
+  void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
+  void *rcoef;                  // real [nc][4]: (a, b, e, 0) of the step l -> l+1
+  void *seedK;                  // real [npairs]: sqrt(binom(2m, m+n))
+  int *pair_off;                // [npairs] entry offset of pair q in the L_J layout
+  int *pair_off0;               // [npairs0] entry offset of pair q in the L0 layout
+  // host copies of the layout
+  int *h_pair_off = nullptr;
+};
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Host-side pair layout: off(m, n) = sum_{m'<m} (2m'+1)(L-m'+1) + (n+m)(L-m+1).
+inline long pair_offset_host(int m, int n, int L) {
+  long o = 0;
+  for (int mm = 0; mm < m; ++mm) o += (long)(2 * mm + 1) * (L - mm + 1);
+  return o + (long)(n + m) * (L - m + 1);
+}
+inline long pair_entries_host(int L) {  // sum_{m<=L} (2m+1)(L-m+1)
+  return pair_offset_host(L + 1, -(L + 1), L) ;
+}
+
+// Table builders (plan_tables.cu).
+cudaError_t build_tables(Plan &p, cudaStream_t st);
+
+// Kernel launchers; each returns cudaGetLastError() after its launches.
+template <typename T>
+cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cudaStream_t st);
+template <typename T>
+cudaError_t launch_correlate(const Plan &p, const T *f, const T *h, int B, int hstride, T *c,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
+                        double *euler, double *score, int *n_cand, cudaStream_t st);
+template <typename T>
+cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
+                          double *score, int *cflags, long long *work, cudaStream_t st);
+cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
+                                const double *cand_euler, const double *cand_score,
+                                const int *cand_flags, double *euler, double *R, double *score,
+                                int *best_p, int *flags, cudaStream_t st);
+
+// Small device helpers.
+template <typename T> struct Cplx { T x, y; };
+
+__device__ __forceinline__ int isqrt_floor(int q) {
+  int m = (int)sqrtf((float)q);
+  while (m * m > q) --m;
+  while ((m + 1) * (m + 1) <= q) ++m;
+  return m;
+}
+
+}  // namespace matcha

@@ -1,0 +1,351 @@
+// The C ABI of include/matcha.h: argument checking, plan construction,
+// workspace carving and the launch sequence of Algorithm 1.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+#include "internal.cuh"
+
+using namespace matcha;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+matcha_status fail_cuda(cudaError_t e, const char *where) {
+  snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+  return MATCHA_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #call); \
+  } while (0)
+
+Plan *P_(matcha_plan p) { return reinterpret_cast<Plan *>(p); }
+
+size_t real_size(const Plan &p) { return p.fp64 ? 8 : 4; }
+
+struct Carve {
+  char *base;
+  size_t off = 0;
+  template <typename X>
+  X *take(size_t count) {
+    X *r = reinterpret_cast<X *>(base + off);
+    off = align_up(off + sizeof(X) * count);
+    return r;
+  }
+};
+
+struct AlignWs {
+  void *f, *h, *c, *grid;
+  int *cidx, *cflags, *ncand;
+  double *ceuler, *cscore;
+};
+
+size_t carve_align(const Plan &p, int B, int Bt, char *base, AlignWs *w) {
+  Carve cv{base};
+  size_t rs = real_size(p);
+  size_t coefv = (size_t)p.S * p.nlm * 2;
+  w->f = cv.take<char>(rs * coefv * B);
+  w->h = cv.take<char>(rs * coefv * Bt);
+  w->c = cv.take<char>(rs * 4 * (size_t)p.nc * B);
+  w->grid = cv.take<char>(rs * (size_t)p.ns * p.ns * p.ns * B);
+  w->cidx = cv.take<int>((size_t)B * p.P);
+  w->cflags = cv.take<int>((size_t)B * p.P);
+  w->ncand = cv.take<int>(B);
+  w->ceuler = cv.take<double>((size_t)B * p.P * 3);
+  w->cscore = cv.take<double>((size_t)B * p.P);
+  return cv.off;
+}
+
+bool valid_stride(int s) { return s == 0 || s == 1; }
+
+}  // namespace
+
+extern "C" {
+
+const char *matcha_status_string(matcha_status s) {
+  switch (s) {
+    case MATCHA_OK: return "ok";
+    case MATCHA_ERR_INVALID_ARG: return "invalid argument";
+    case MATCHA_ERR_CUDA: return "CUDA error";
+    case MATCHA_ERR_WORKSPACE: return "workspace too small";
+    case MATCHA_ERR_TIMEOUT: return "device wait timed out";
+    case MATCHA_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *matcha_last_error(void) { return g_err; }
+
+matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
+  if (!d || !out) return MATCHA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->box_n < 4 || d->box_n > 512 || d->n_shells < 1 || d->n_shells > 128) return MATCHA_ERR_INVALID_ARG;
+  if (d->L0 < 1 || d->L0 > 32 || d->K_oversample < 1 || d->K_oversample > 4) return MATCHA_ERR_INVALID_ARG;
+  if (d->P_max < 1 || d->P_max > MATCHA_MAX_P || d->M_iter < 1 || d->M_iter > 32) return MATCHA_ERR_INVALID_ARG;
+  if (d->n_levels < 1 || d->n_levels > MATCHA_MAX_LEVELS) return MATCHA_ERR_INVALID_ARG;
+  if (d->L_sched[0] != d->L0) return MATCHA_ERR_INVALID_ARG;
+  for (int i = 1; i < d->n_levels; ++i)
+    if (d->L_sched[i] <= d->L_sched[i - 1]) return MATCHA_ERR_INVALID_ARG;
+  if (d->L_sched[d->n_levels - 1] > MATCHA_MAX_L) return MATCHA_ERR_UNSUPPORTED;
+  if (d->precision != MATCHA_FP64 && d->precision != MATCHA_FP32) return MATCHA_ERR_INVALID_ARG;
+  if (!(isfinite(d->r_max)) || !(isfinite(d->step_tol))) return MATCHA_ERR_INVALID_ARG;
+
+  Plan *p = new Plan();
+  p->desc = *d;
+  p->N = d->box_n; p->S = d->n_shells; p->L0 = d->L0; p->K = d->K_oversample;
+  p->P = d->P_max; p->M = d->M_iter; p->nlev = d->n_levels;
+  for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) p->Ls[i] = i < d->n_levels ? d->L_sched[i] : 0;
+  p->LJ = d->L_sched[d->n_levels - 1];
+  p->R = d->r_max > 0 ? d->r_max : 0.5 * d->box_n - 1.0;
+  p->fp64 = d->precision == MATCHA_FP64;
+  p->step_tol = d->step_tol > 0 ? d->step_tol : (p->fp64 ? 1e-9 : 1e-6);
+  p->nt = p->LJ + 1;
+  p->np = 2 * p->LJ + 2;
+  p->nlm = (p->LJ + 1) * (p->LJ + 2) / 2;
+  p->npairs = (p->LJ + 1) * (p->LJ + 1);
+  p->npairs0 = (p->L0 + 1) * (p->L0 + 1);
+  p->ns = 2 * p->K * (p->L0 + 1);
+  p->nc = pair_entries_host(p->LJ);
+  p->nc0 = pair_entries_host(p->L0);
+  std::vector<int> off(p->npairs), off0(p->npairs0);
+  for (int m = 0; m <= p->LJ; ++m)
+    for (int n = -m; n <= m; ++n) {
+      int q = m * m + n + m;
+      off[q] = (int)pair_offset_host(m, n, p->LJ);
+      if (m <= p->L0) off0[q] = (int)pair_offset_host(m, n, p->L0);
+    }
+  size_t rs = real_size(*p);
+  size_t sz = 0;
+  auto add = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes); return o; };
+  size_t o_rs = add(8 * p->S), o_w = add(8 * p->S), o_x = add(8 * p->nt), o_wj = add(8 * p->nt);
+  size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
+  size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * p->npairs);
+  size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
+  cudaError_t e = cudaMalloc(&p->base, sz);
+  if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
+  char *b = (char *)p->base;
+  p->rs = (double *)(b + o_rs); p->wrad = (double *)(b + o_w);
+  p->xj = (double *)(b + o_x); p->wj = (double *)(b + o_wj);
+  p->ptab = b + o_pt; p->phi_cs = b + o_phi; p->soft_tw = b + o_tw; p->soft_d = b + o_sd;
+  p->rcoef = b + o_rc; p->seedK = b + o_K;
+  p->pair_off = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
+  p->h_pair_off = new int[p->npairs];
+  memcpy(p->h_pair_off, off.data(), sizeof(int) * p->npairs);
+  e = cudaMemcpy(p->pair_off, off.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = build_tables(*p, 0);
+  if (e != cudaSuccess) {
+    cudaFree(p->base);
+    delete[] p->h_pair_off;
+    delete p;
+    return fail_cuda(e, "plan tables");
+  }
+  *out = reinterpret_cast<matcha_plan>(p);
+  return MATCHA_OK;
+}
+
+matcha_status matcha_plan_destroy(matcha_plan plan) {
+  if (!plan) return MATCHA_OK;
+  Plan *p = P_(plan);
+  cudaDeviceSynchronize();
+  cudaError_t e = cudaFree(p->base);
+  delete[] p->h_pair_off;
+  delete p;
+  if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info) {
+  if (!plan || !info) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  info->n_lm = p->nlm;
+  info->coeff_count = (long)p->S * p->nlm;
+  info->corr_entries = p->nc;
+  info->n_pairs = p->npairs;
+  info->soft_n = p->ns;
+  info->real_bytes = (int)real_size(*p);
+  return MATCHA_OK;
+}
+
+matcha_status matcha_plan_table(matcha_plan plan, int which, double *host_out, long capacity,
+                                long *count) {
+  if (!plan || !count || capacity < 0) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  const double *src;
+  long n;
+  switch (which) {
+    case 0: src = p->rs; n = p->S; break;
+    case 1: src = p->wrad; n = p->S; break;
+    case 2: src = p->xj; n = p->nt; break;
+    case 3: src = p->wj; n = p->nt; break;
+    default: return MATCHA_ERR_INVALID_ARG;
+  }
+  *count = n;
+  if (host_out && capacity > 0) {
+    long k = capacity < n ? capacity : n;
+    CK(cudaMemcpy(host_out, src, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  }
+  return MATCHA_OK;
+}
+
+matcha_status matcha_workspace_size(matcha_plan plan, int B, size_t *bytes) {
+  if (!plan || !bytes || B < 0) return MATCHA_ERR_INVALID_ARG;
+  AlignWs w;
+  *bytes = carve_align(*P_(plan), B, B, nullptr, &w);
+  return MATCHA_OK;
+}
+
+matcha_status matcha_analyze(matcha_plan plan, const float *vols, int B, void *coeffs, void *stream) {
+  if (!plan || B < 0 || (B > 0 && (!vols || !coeffs))) return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  Plan *p = P_(plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p->fp64 ? launch_analyze<double>(*p, vols, B, (double *)coeffs, st)
+                          : launch_analyze<float>(*p, vols, B, (float *)coeffs, st);
+  if (e != cudaSuccess) return fail_cuda(e, "analyze");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_correlate_coeffs(matcha_plan plan, const void *f, const void *h, int B,
+                                      int h_batch_stride, void *c, void *stream) {
+  if (!plan || B < 0 || !valid_stride(h_batch_stride) || (B > 0 && (!f || !h || !c)))
+    return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  Plan *p = P_(plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p->fp64 ? launch_correlate<double>(*p, (const double *)f, (const double *)h, B,
+                                                     h_batch_stride, (double *)c, st)
+                          : launch_correlate<float>(*p, (const float *)f, (const float *)h, B,
+                                                    h_batch_stride, (float *)c, st);
+  if (e != cudaSuccess) return fail_cuda(e, "correlate_coeffs");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_soft_search(matcha_plan plan, const void *c, int B, const int *P_per,
+                                 void *grid, int *idx, double *euler, double *score, int *n_cand,
+                                 void *stream) {
+  if (!plan || B < 0 || (B > 0 && (!c || !grid || !idx || !euler || !score || !n_cand)))
+    return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  Plan *p = P_(plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p->fp64 ? launch_soft<double>(*p, (const double *)c, B, P_per, (double *)grid,
+                                                idx, euler, score, n_cand, st)
+                          : launch_soft<float>(*p, (const float *)c, B, P_per, (float *)grid, idx,
+                                               euler, score, n_cand, st);
+  if (e != cudaSuccess) return fail_cuda(e, "soft_search");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_newton_march(matcha_plan plan, const void *c, int B, const int *n_cand,
+                                  double *euler, double *score, int *cflags, long long *work,
+                                  void *stream) {
+  if (!plan || B < 0 || (B > 0 && (!c || !n_cand || !euler || !score || !cflags)))
+    return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p->fp64 ? launch_newton<double>(*p, (const double *)c, B, n_cand, euler, score,
+                                                  cflags, work, st)
+                          : launch_newton<float>(*p, (const float *)c, B, n_cand, euler, score,
+                                                 cflags, work, st);
+  if (e != cudaSuccess) return fail_cuda(e, "newton_march");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per, const int *n_cand,
+                                  const double *cand_euler, const double *cand_score,
+                                  const int *cand_flags, double *euler, double *R, double *score,
+                                  int *best_p, int *flags, void *stream) {
+  if (!plan || B < 0 || (B > 0 && (!n_cand || !cand_euler || !cand_score || !cand_flags || !euler ||
+                                   !R || !score || !best_p || !flags)))
+    return MATCHA_ERR_INVALID_ARG;
+  cudaError_t e = launch_final_select(*P_(plan), B, P_per, n_cand, cand_euler, cand_score,
+                                      cand_flags, euler, R, score, best_p, flags,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(e, "final_select");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_align(matcha_plan plan, const float *particles, const float *templates, int B,
+                           int tstride, const int *P_per, double *euler, double *R, double *score,
+                           int *best_p, int *flags, void *ws, size_t ws_bytes, void *stream) {
+  if (!plan || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  if (B == 0) return MATCHA_OK;
+  if (!particles || !templates || !euler || !R || !score || !best_p || !flags || !ws)
+    return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  const int Bt = tstride ? B : 1;
+  AlignWs w;
+  size_t need = carve_align(*p, B, Bt, (char *)ws, &w);
+  if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
+  matcha_status s;
+  if ((s = matcha_analyze(plan, particles, B, w.f, stream))) return s;
+  if ((s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
+  if ((s = matcha_correlate_coeffs(plan, w.f, w.h, B, tstride, w.c, stream))) return s;
+  if ((s = matcha_soft_search(plan, w.c, B, P_per, w.grid, w.cidx, w.ceuler, w.cscore, w.ncand,
+                              stream)))
+    return s;
+  if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags, nullptr,
+                               stream)))
+    return s;
+  return matcha_final_select(plan, B, P_per, w.ncand, w.ceuler, w.cscore, w.cflags, euler, R, score,
+                             best_p, flags, stream);
+}
+
+matcha_status matcha_host_workspace_size(matcha_plan plan, int B, int tstride, size_t *bytes) {
+  if (!plan || !bytes || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  AlignWs w;
+  const int Bt = tstride ? B : 1;
+  size_t vox = (size_t)p->N * p->N * p->N;
+  size_t sz = align_up(carve_align(*p, B, Bt, nullptr, &w));
+  sz += align_up(sizeof(float) * vox * B) + align_up(sizeof(float) * vox * Bt);
+  sz += align_up(sizeof(double) * 13 * B) + align_up(sizeof(int) * 2 * B);
+  *bytes = sz;
+  return MATCHA_OK;
+}
+
+matcha_status matcha_align_host(matcha_plan plan, const float *particles, const float *templates,
+                                int B, int tstride, double *euler, double *R, double *score,
+                                int *best_p, int *flags, void *ws, size_t ws_bytes, void *stream) {
+  if (!plan || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  if (B == 0) return MATCHA_OK;
+  if (!particles || !templates || !euler || !R || !score || !best_p || !flags || !ws)
+    return MATCHA_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+  size_t need;
+  matcha_status s = matcha_host_workspace_size(plan, B, tstride, &need);
+  if (s) return s;
+  if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
+  Plan *p = P_(plan);
+  const int Bt = tstride ? B : 1;
+  AlignWs w;
+  size_t inner = align_up(carve_align(*p, B, Bt, nullptr, &w));
+  Carve cv{(char *)ws + inner};
+  size_t vox = (size_t)p->N * p->N * p->N;
+  float *dpart = cv.take<float>(vox * B);
+  float *dtemp = cv.take<float>(vox * Bt);
+  double *dout = cv.take<double>(13 * (size_t)B);
+  int *iout = cv.take<int>(2 * (size_t)B);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(dpart, particles, sizeof(float) * vox * B, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dtemp, templates, sizeof(float) * vox * Bt, cudaMemcpyHostToDevice, st));
+  s = matcha_align(plan, dpart, dtemp, B, tstride, nullptr, dout, dout + 3 * B, dout + 12 * B, iout,
+                   iout + B, ws, inner, stream);
+  if (s) return s;
+  CK(cudaMemcpyAsync(euler, dout, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(R, dout + 3 * B, sizeof(double) * 9 * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(score, dout + 12 * B, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(best_p, iout, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(flags, iout + B, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MATCHA_OK;
+}
+
+}  // extern "C"

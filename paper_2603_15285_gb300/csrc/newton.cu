@@ -1,0 +1,514 @@
+// Step a6: frequency-marched Newton refinement (Sections 2.2-2.4, Algorithm 1)
+// and step a7: the final argmax over candidates.
+//
+// C_L(a,b,g) = Re sum_{l<=L} sum_{m,n} c^l_{mn} e^{i(m a + n g)} d^l_{mn}(b),
+// grad and Hessian in (a, b, g): d/da brings i m, d/dg brings i n, d/db acts
+// on d^l (Appendix A.4).  Every evaluation runs the three-term l-recurrence
+// of d, d' and d'' for each order pair (m, n) with m >= |n| and uses
+//   d^l_{nm} = (-1)^{m-n} d^l_{mn}            (transposed image),
+//   term(-m,-n) = conj(term(m,n))              (real volumes),
+// so one recurrence serves the four orders (m,n), (n,m), (-m,-n), (-n,-m).
+//
+// Work layout: one CTA per particle holds all P candidates.  A warp is split
+// into sub-slots of `cpw` lanes (cpw = P rounded up to a power of two); lane
+// p of a sub-slot follows candidate p, and a sub-slot walks one order pair at
+// a time, so the coefficient loads c^l and the recurrence coefficients of a
+// step are warp broadcasts.  Per-lane partial sums are reduced in a fixed
+// order (shuffles, then warps in index order, in FP64), so results do not
+// depend on scheduling.
+//
+// Step rule (the paper gives only the plain update theta - H^{-1} grad):
+//   delta = -H^{-1} grad when -H is positive definite (Cholesky pivots
+//   > 1e-12 ||H||_F), else grad / ||H||_F (flag bit 1); ||delta|| clamped to
+//   pi / (2 (L+1)); the level ends early when ||delta|| < step_tol
+//   (Section 2.4); trial theta' = wrap(theta + delta) is accepted when
+//   C(theta') >= C(theta), else delta is halved (at most twice); three
+//   rejected trials end the level for that candidate (flag bit 2), since a
+//   repeated step from the same point would reject again.  Angles, the 3x3
+//   solve and the acceptance test are FP64 in both precisions.
+#include <math.h>
+#include "internal.cuh"
+
+namespace matcha {
+
+constexpr int NEWTON_THREADS = 256;
+constexpr int NEWTON_WARPS = NEWTON_THREADS / 32;
+
+enum { ST_RUN = 0, ST_TRIAL = 1, ST_STOP = 2, ST_DEAD = 3 };
+
+struct NewtonArgs {
+  int LJ, nlev, M, P, cpw;
+  int Ls[MATCHA_MAX_LEVELS];
+  double tol;
+  long nc;
+};
+
+template <typename T>
+__device__ __forceinline__ T ipow_t(T x, int e) {
+  T r = T(1);
+  while (e) {
+    if (e & 1) r *= x;
+    x *= x;
+    e >>= 1;
+  }
+  return r;
+}
+
+template <typename T> __device__ __forceinline__ T tcos(T x);
+template <typename T> __device__ __forceinline__ T tsin(T x);
+template <> __device__ __forceinline__ float tcos<float>(float x) { return cosf(x); }
+template <> __device__ __forceinline__ float tsin<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double tcos<double>(double x) { return cos(x); }
+template <> __device__ __forceinline__ double tsin<double>(double x) { return sin(x); }
+
+struct SmemLayout {
+  double *th, *tr, *del, *Cc, *res, *red;
+  int *state, *steps, *tries, *fl;
+  void *evp, *ea, *eg;
+};
+
+// Accumulates the contributions of one order pair for one candidate.
+template <typename T, bool FULL>
+__device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__restrict__ rp, T K,
+                                         int m, int n, int L, T x, T s, T ch, T sh, T *A) {
+  // seed at l = m: d = sigma K ch^a sh^b, a = m+n, b = m-n, sigma = (-1)^b
+  const int a = m + n, bq = m - n;
+  T c_a = ipow_t(ch, a), s_b = ipow_t(sh, bq);
+  T sg = (bq & 1) ? T(-1) : T(1);
+  T d0 = sg * K * c_a * s_b, d1 = 0, d2 = 0;
+  if (FULL) {
+    // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2, and the
+    // second derivative from differentiating once more.
+    T c_am1 = a >= 1 ? ipow_t(ch, a - 1) : T(0);
+    T c_am2 = a >= 2 ? ipow_t(ch, a - 2) : T(0);
+    T s_bm1 = bq >= 1 ? ipow_t(sh, bq - 1) : T(0);
+    T s_bm2 = bq >= 2 ? ipow_t(sh, bq - 2) : T(0);
+    T c_ap1 = c_a * ch, c_ap2 = c_ap1 * ch, s_bp1 = s_b * sh, s_bp2 = s_bp1 * sh;
+    T gK = sg * K;
+    d1 = gK * T(0.5) * (T(bq) * c_ap1 * s_bm1 - T(a) * c_am1 * s_bp1);
+    d2 = gK * T(0.25) *
+         (T(bq * (bq - 1)) * c_ap2 * s_bm2 - T(bq * (a + 1) + a * (bq + 1)) * c_a * s_b +
+          T(a * (a - 1)) * c_am2 * s_bp2);
+  }
+  T p0 = 0, p1 = 0, p2 = 0;  // previous-degree values
+  T a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
+  T b0r = 0, b0i = 0, b1r = 0, b1i = 0, b2r = 0, b2i = 0;
+  for (int l = m;; ++l) {
+    const T *e = cp + 4 * (l - m);
+    T cr = e[0], ci = e[1], dr = e[2], di = e[3];
+    a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
+    b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
+    if (FULL) {
+      a1r = fma(cr, d1, a1r); a1i = fma(ci, d1, a1i);
+      b1r = fma(dr, d1, b1r); b1i = fma(di, d1, b1i);
+      a2r = fma(cr, d2, a2r); a2i = fma(ci, d2, a2i);
+      b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
+    }
+    if (l == L) break;
+    const T *r = rp + 4 * (l - m);
+    T ca = r[0], cb = r[1], ce = r[2];
+    T t = fma(ca, x, -cb);
+    T n0 = fma(t, d0, -ce * p0);
+    if (FULL) {
+      T as = ca * s;
+      T n1 = fma(t, d1, -fma(as, d0, ce * p1));
+      T n2 = fma(t, d2, -fma(as + as, d1, fma(ca * x, d0, ce * p2)));
+      p1 = d1; d1 = n1;
+      p2 = d2; d2 = n2;
+    }
+    p0 = d0; d0 = n0;
+  }
+  A[0] = a0r; A[1] = a0i; A[2] = b0r; A[3] = b0i;
+  if (FULL) {
+    A[4] = a1r; A[5] = a1i; A[6] = b1r; A[7] = b1i;
+    A[8] = a2r; A[9] = a2i; A[10] = b2r; A[11] = b2i;
+  }
+}
+
+template <typename T, bool FULL>
+__device__ __forceinline__ void add_image(T *acc, T w, int a, int b, T zr0, T zi0, T zr1, T zi1,
+                                          T zr2) {
+  acc[0] += w * zr0;
+  if (FULL) {
+    T fa = T(a), fb = T(b);
+    acc[1] += w * (-fa * zi0);
+    acc[2] += w * zr1;
+    acc[3] += w * (-fb * zi0);
+    acc[4] += w * (-fa * fa * zr0);
+    acc[5] += w * (-fa * zi1);
+    acc[6] += w * (-fa * fb * zr0);
+    acc[7] += w * zr2;
+    acc[8] += w * (-fb * zi1);
+    acc[9] += w * (-fb * fb * zr0);
+  }
+}
+
+// Evaluates C (and grad, Hessian when FULL) at pts[p] for the candidates with
+// need[p] != 0; results in res[p][0..9] (FP64).  Called by the whole CTA.
+template <typename T, bool FULL>
+__device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
+                         const int *__restrict__ pair_off, const T *__restrict__ rcoef,
+                         const T *__restrict__ seedK, const double *pts, const int *need,
+                         SmemLayout &sm) {
+  const int P = A.P, cpw = A.cpw, W = 2 * L + 1;
+  T *evp = (T *)sm.evp;  // [P][8]: x, s, ch, sh, cos a, sin a, cos g, sin g
+  T *ea = (T *)sm.ea;    // [P][W][2]: e^{i m a}, m = -L..L
+  T *eg = (T *)sm.eg;
+  const int tid = threadIdx.x;
+  if (tid < P && need[tid]) {
+    T al = (T)pts[3 * tid], be = (T)pts[3 * tid + 1], ga = (T)pts[3 * tid + 2];
+    T *e = evp + 8 * tid;
+    e[0] = tcos(be); e[1] = tsin(be);
+    e[2] = tcos(be * T(0.5)); e[3] = tsin(be * T(0.5));
+    e[4] = tcos(al); e[5] = tsin(al);
+    e[6] = tcos(ga); e[7] = tsin(ga);
+  }
+  __syncthreads();
+  if (tid < 2 * P) {
+    int p = tid >> 1, which = tid & 1;
+    if (need[p]) {
+      T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
+      T *tab = (which ? eg : ea) + 2 * (long)p * W;
+      T cr = 1, ci = 0;
+      tab[2 * L] = 1; tab[2 * L + 1] = 0;
+      for (int m = 1; m <= L; ++m) {
+        T nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+        cr = nr; ci = ni;
+        tab[2 * (L + m)] = cr; tab[2 * (L + m) + 1] = ci;
+        tab[2 * (L - m)] = cr; tab[2 * (L - m) + 1] = -ci;
+      }
+    }
+  }
+  __syncthreads();
+
+  const int lane = tid & 31, warp = tid >> 5;
+  const int spw = 32 / cpw;
+  const int p = lane & (cpw - 1);
+  const int slot = warp * spw + lane / cpw;
+  const int nslots = NEWTON_WARPS * spw;
+  const bool act = p < P && need[p];
+  T acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = 0;
+  if (act) {
+    const T *e = evp + 8 * p;
+    T x = e[0], s = e[1], ch = e[2], sh = e[3];
+    const T *eap = ea + 2 * (long)p * W, *egp = eg + 2 * (long)p * W;
+    const int npl = (L + 1) * (L + 1);
+    for (int q = slot; q < npl; q += nslots) {
+      int m = isqrt_floor(q), n = q - m * m - m;
+      int off = pair_off[q];
+      T Acc[12];
+      pair_sum<T, FULL>(cb + 4L * off, rcoef + 4L * off, seedK[q], m, n, L, x, s, ch, sh, Acc);
+      // image (m, n) and its negation
+      {
+        T er = eap[2 * (m + L)] * egp[2 * (n + L)] - eap[2 * (m + L) + 1] * egp[2 * (n + L) + 1];
+        T ei = eap[2 * (m + L)] * egp[2 * (n + L) + 1] + eap[2 * (m + L) + 1] * egp[2 * (n + L)];
+        T w = q == 0 ? T(1) : T(2);
+        T zr0 = Acc[0] * er - Acc[1] * ei, zi0 = Acc[0] * ei + Acc[1] * er;
+        T zr1 = 0, zi1 = 0, zr2 = 0;
+        if (FULL) {
+          zr1 = Acc[4] * er - Acc[5] * ei; zi1 = Acc[4] * ei + Acc[5] * er;
+          zr2 = Acc[8] * er - Acc[9] * ei;
+        }
+        add_image<T, FULL>(acc, w, m, n, zr0, zi0, zr1, zi1, zr2);
+      }
+      if (n != m && n != -m) {
+        // image (n, m): c^l_nm d^l_nm e^{i(n a + m g)}, d^l_nm = (-1)^{m-n} d^l_mn
+        T sg = ((m - n) & 1) ? T(-2) : T(2);
+        T er = eap[2 * (n + L)] * egp[2 * (m + L)] - eap[2 * (n + L) + 1] * egp[2 * (m + L) + 1];
+        T ei = eap[2 * (n + L)] * egp[2 * (m + L) + 1] + eap[2 * (n + L) + 1] * egp[2 * (m + L)];
+        T zr0 = Acc[2] * er - Acc[3] * ei, zi0 = Acc[2] * ei + Acc[3] * er;
+        T zr1 = 0, zi1 = 0, zr2 = 0;
+        if (FULL) {
+          zr1 = Acc[6] * er - Acc[7] * ei; zi1 = Acc[6] * ei + Acc[7] * er;
+          zr2 = Acc[10] * er - Acc[11] * ei;
+        }
+        add_image<T, FULL>(acc, sg, n, m, zr0, zi0, zr1, zi1, zr2);
+      }
+    }
+  }
+  // reduce over the sub-slots of the warp that follow the same candidate
+  const int nq = FULL ? 10 : 1;
+  double accd[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) accd[i] = (double)acc[i];
+  for (int o = cpw; o < 32; o <<= 1)
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+      if (i < nq) accd[i] += __shfl_xor_sync(0xffffffffu, accd[i], o);
+  if (lane < cpw && p < P)
+    for (int i = 0; i < nq; ++i) sm.red[(warp * P + p) * 10 + i] = accd[i];
+  __syncthreads();
+  for (int idx = tid; idx < P * nq; idx += blockDim.x) {
+    int pp = idx / nq, i = idx - pp * nq;
+    if (need[pp]) {
+      double v = 0;
+      for (int w = 0; w < NEWTON_WARPS; ++w) v += sm.red[(w * P + pp) * 10 + i];
+      sm.res[pp * 10 + i] = v;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ double mod2pi_d(double x) {
+  const double t = 2.0 * M_PI;
+  double r = x - t * floor(x / t);
+  if (r >= t) r -= t;
+  if (r < 0) r += t;
+  return r;
+}
+
+__device__ void wrap_d(double *v) {
+  double a = v[0], b = v[1], g = v[2];
+  if (b < 0) { b = -b; a += M_PI; g += M_PI; }
+  else if (b > M_PI) { b = 2.0 * M_PI - b; a += M_PI; g += M_PI; }
+  v[0] = mod2pi_d(a); v[1] = b; v[2] = mod2pi_d(g);
+}
+
+// Newton direction from grad g and Hessian H (row-major 3x3); returns flag bits.
+__device__ int newton_dir(const double *g, const double *H, int L, double *d) {
+  double hn = 0;
+  for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
+  hn = sqrt(hn);
+  const double tol = 1e-12 * hn;
+  // Cholesky of A = -H
+  double a00 = -H[0], a10 = -H[3], a20 = -H[6], a11 = -H[4], a21 = -H[7], a22 = -H[8];
+  bool ok = a00 > tol;
+  double L00 = 0, L10 = 0, L20 = 0, L11 = 0, L21 = 0, L22 = 0;
+  if (ok) {
+    L00 = sqrt(a00); L10 = a10 / L00; L20 = a20 / L00;
+    double p11 = a11 - L10 * L10;
+    ok = p11 > tol;
+    if (ok) {
+      L11 = sqrt(p11); L21 = (a21 - L20 * L10) / L11;
+      double p22 = a22 - L20 * L20 - L21 * L21;
+      ok = p22 > tol;
+      if (ok) L22 = sqrt(p22);
+    }
+  }
+  int fl = 0;
+  if (ok) {
+    double y0 = g[0] / L00;
+    double y1 = (g[1] - L10 * y0) / L11;
+    double y2 = (g[2] - L20 * y0 - L21 * y1) / L22;
+    double x2 = y2 / L22;
+    double x1 = (y1 - L21 * x2) / L11;
+    double x0 = (y0 - L10 * x1 - L20 * x2) / L00;
+    d[0] = x0; d[1] = x1; d[2] = x2;
+  } else {
+    fl = 2;
+    for (int i = 0; i < 3; ++i) d[i] = hn > 0 ? g[i] / hn : 0.0;
+  }
+  double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double cap = M_PI / (2.0 * (L + 1.0));
+  if (nrm > cap)
+    for (int i = 0; i < 3; ++i) d[i] *= cap / nrm;
+  return fl;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NEWTON_THREADS)
+k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__restrict__ rcoef,
+         const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
+         double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
+         long long *__restrict__ work) {
+  const long b = blockIdx.x;
+  const int P = A.P, tid = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemLayout sm;
+  double *dp = reinterpret_cast<double *>(smem_raw);
+  sm.th = dp; dp += 3 * P;
+  sm.tr = dp; dp += 3 * P;
+  sm.del = dp; dp += 3 * P;
+  sm.Cc = dp; dp += P;
+  sm.res = dp; dp += 10 * P;
+  sm.red = dp; dp += 10 * P * NEWTON_WARPS;
+  int *ip = reinterpret_cast<int *>(dp);
+  sm.state = ip; ip += P;
+  sm.steps = ip; ip += P;
+  sm.tries = ip; ip += P;
+  sm.fl = ip; ip += P;
+  int *need = ip; ip += P;
+  uintptr_t u = reinterpret_cast<uintptr_t>(ip);
+  u = (u + 15) & ~uintptr_t(15);
+  T *tp = reinterpret_cast<T *>(u);
+  const int Wm = 2 * A.LJ + 1;
+  sm.evp = tp; tp += 8 * P;
+  sm.ea = tp; tp += 2 * P * Wm;
+  sm.eg = tp; tp += 2 * P * Wm;
+
+  const int nc_b = n_cand[b];
+  if (tid < P) {
+    double *e = euler + 3 * (b * P + tid);
+    sm.th[3 * tid] = e[0]; sm.th[3 * tid + 1] = e[1]; sm.th[3 * tid + 2] = e[2];
+    sm.state[tid] = tid < nc_b ? ST_RUN : ST_DEAD;
+    sm.fl[tid] = 0;
+    sm.Cc[tid] = __longlong_as_double(0x7ff8000000000000LL);
+  }
+  __syncthreads();
+  const T *cb = c + 4 * b * A.nc;
+  long long work_full = 0, work_val = 0;  // counted by thread 0
+
+  for (int lev = 0; lev < A.nlev; ++lev) {
+    const int L = A.Ls[lev];
+    // recurrence steps of one evaluation: sum_{m<=L} (2m+1)(L-m+1)
+    long long steps_L = 0;
+    for (int mm = 0; mm <= L; ++mm) steps_L += (long long)(2 * mm + 1) * (L - mm + 1);
+    if (tid < P && sm.state[tid] != ST_DEAD) sm.state[tid] = ST_RUN;
+    __syncthreads();
+    for (int t = 0; t < A.M; ++t) {
+      int want = 0;
+      if (tid < P) { need[tid] = sm.state[tid] == ST_RUN; want = need[tid]; }
+      if (!__syncthreads_or(want)) break;
+      if (tid == 0)
+        for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
+      evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
+      if (tid < P && need[tid]) {
+        const double *r = sm.res + 10 * tid;
+        double C = r[0], g[3] = {r[1], r[2], r[3]};
+        double H[9] = {r[4], r[5], r[6], r[5], r[7], r[8], r[6], r[8], r[9]};
+        bool fin = isfinite(C);
+        for (int i = 0; i < 3; ++i) fin = fin && isfinite(g[i]);
+        for (int i = 0; i < 9; ++i) fin = fin && isfinite(H[i]);
+        sm.Cc[tid] = C;
+        if (!fin) {
+          sm.fl[tid] |= 1;
+          sm.state[tid] = ST_DEAD;
+        } else {
+          double d[3];
+          sm.fl[tid] |= newton_dir(g, H, L, d);
+          if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < A.tol) {
+            sm.state[tid] = ST_STOP;
+          } else {
+            for (int i = 0; i < 3; ++i) { sm.del[3 * tid + i] = d[i]; }
+            double tr[3] = {sm.th[3 * tid] + d[0], sm.th[3 * tid + 1] + d[1], sm.th[3 * tid + 2] + d[2]};
+            wrap_d(tr);
+            for (int i = 0; i < 3; ++i) sm.tr[3 * tid + i] = tr[i];
+            sm.tries[tid] = 0;
+            sm.state[tid] = ST_TRIAL;
+          }
+        }
+      }
+      for (int h = 0; h < 3; ++h) {
+        int tw = 0;
+        if (tid < P) { need[tid] = sm.state[tid] == ST_TRIAL; tw = need[tid]; }
+        if (!__syncthreads_or(tw)) break;
+        if (tid == 0)
+          for (int q = 0; q < P; ++q) work_val += need[q] ? steps_L : 0;
+        evaluate<T, false>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+        if (tid < P && need[tid]) {
+          double Ct = sm.res[10 * tid];
+          if (Ct >= sm.Cc[tid]) {
+            for (int i = 0; i < 3; ++i) sm.th[3 * tid + i] = sm.tr[3 * tid + i];
+            sm.Cc[tid] = Ct;
+            sm.state[tid] = ST_RUN;
+          } else if (++sm.tries[tid] == 3) {
+            sm.fl[tid] |= 4;
+            sm.state[tid] = ST_STOP;
+          } else {
+            double tr[3];
+            for (int i = 0; i < 3; ++i) {
+              sm.del[3 * tid + i] *= 0.5;
+              tr[i] = sm.th[3 * tid + i] + sm.del[3 * tid + i];
+            }
+            wrap_d(tr);
+            for (int i = 0; i < 3; ++i) sm.tr[3 * tid + i] = tr[i];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < P) {
+    long o = b * P + tid;
+    if (tid < nc_b) {
+      euler[3 * o] = sm.th[3 * tid];
+      euler[3 * o + 1] = sm.th[3 * tid + 1];
+      euler[3 * o + 2] = sm.th[3 * tid + 2];
+      score[o] = sm.Cc[tid];
+    }
+    cflags[o] = sm.fl[tid];
+  }
+  if (tid == 0 && work) {
+    work[2 * b] = work_full;
+    work[2 * b + 1] = work_val;
+  }
+}
+
+size_t newton_smem_bytes(const Plan &p, size_t tsize) {
+  size_t P = p.P, W = 2 * p.LJ + 1;
+  size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
+  bytes += sizeof(int) * 5 * P;
+  bytes = (bytes + 15) / 16 * 16;
+  bytes += tsize * (8 * P + 4 * P * W);
+  return bytes;
+}
+
+template <typename T>
+cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
+                          double *score, int *cflags, long long *work, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  NewtonArgs A;
+  A.LJ = p.LJ; A.nlev = p.nlev; A.M = p.M; A.P = p.P;
+  int cpw = 1;
+  while (cpw < p.P) cpw <<= 1;
+  A.cpw = cpw;
+  for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
+  A.tol = p.step_tol;
+  A.nc = p.nc;
+  size_t smem = newton_smem_bytes(p, sizeof(T));
+  cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_newton<T><<<B, NEWTON_THREADS, smem, st>>>(c, p.pair_off, (const T *)p.rcoef,
+                                               (const T *)p.seedK, A, n_cand, euler, score, cflags,
+                                               work);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_newton<float>(const Plan &, const float *, int, const int *, double *,
+                                          double *, int *, long long *, cudaStream_t);
+template cudaError_t launch_newton<double>(const Plan &, const double *, int, const int *, double *,
+                                           double *, int *, long long *, cudaStream_t);
+
+__global__ void k_final_select(int B, int P, const int *P_per, const int *n_cand,
+                               const double *ce, const double *cs, const int *cf, double *euler,
+                               double *R, double *score, int *best_p, int *flags) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int nc = n_cand[b];
+  int Pb = P_per ? min(P_per[b], P) : P;
+  int best = -1, fl = nc < Pb ? 8 : 0;
+  double bs = -INFINITY;
+  for (int q = 0; q < nc; ++q) {
+    double s = cs[(long)b * P + q];
+    fl |= cf[(long)b * P + q];
+    if (s > bs) { bs = s; best = q; }
+  }
+  double a = 0, be = 0, g = 0;
+  if (best >= 0) {
+    const double *e = ce + 3 * ((long)b * P + best);
+    a = e[0]; be = e[1]; g = e[2];
+  }
+  euler[3 * b] = a; euler[3 * b + 1] = be; euler[3 * b + 2] = g;
+  // R = r_z(a) r_y(b) r_z(g)
+  double ca = cos(a), sa = sin(a), cb = cos(be), sb = sin(be), cg = cos(g), sg = sin(g);
+  double *r = R + 9 * b;
+  r[0] = ca * cb * cg - sa * sg; r[1] = -ca * cb * sg - sa * cg; r[2] = ca * sb;
+  r[3] = sa * cb * cg + ca * sg; r[4] = -sa * cb * sg + ca * cg; r[5] = sa * sb;
+  r[6] = -sb * cg;               r[7] = sb * sg;                 r[8] = cb;
+  score[b] = best >= 0 ? bs : __longlong_as_double(0x7ff8000000000000LL);
+  best_p[b] = best;
+  flags[b] = fl;
+}
+
+cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
+                                const double *cand_euler, const double *cand_score,
+                                const int *cand_flags, double *euler, double *R, double *score,
+                                int *best_p, int *flags, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  k_final_select<<<(B + 127) / 128, 128, 0, st>>>(B, p.P, P_per, n_cand, cand_euler, cand_score,
+                                                  cand_flags, euler, R, score, best_p, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace matcha

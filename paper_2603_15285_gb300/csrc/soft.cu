@@ -1,0 +1,221 @@
+// Steps a4+a5: the SOFFT initialisation (Section 2.3; Algorithm 1, steps 1-2).
+//
+// C_{L0} on the equiangular grid alpha_i = 2 pi i/n, beta_k = pi(2k+1)/(2n),
+// gamma_j = 2 pi j/n, n = 2K(L0+1), is evaluated as the inverse SO(3) Fourier
+// transform of Kostelec and Rockmore:
+//   S_mn(beta_k)   = sum_{l=max(|m|,|n|)}^{L0} c^l_{mn} d^l_{mn}(beta_k)   (beta transform)
+//   C(a_i,b_k,g_j) = Re sum_{m,n} S_mn(beta_k) e^{i(m a_i + n g_j)}       (2-D DFT)
+// For real volumes S_{-m,-n} = conj(S_mn), so the alpha sum folds to
+// m >= 0.  One CTA per (beta_k, particle).
+//
+// Candidates: a grid point is a local maximum when it precedes all 26
+// neighbours in the order (value desc, index asc), alpha and gamma wrapping
+// and beta neighbours outside the grid skipped; the P strongest local maxima
+// in that order are kept.  One CTA per particle compacts the local maxima
+// into shared memory and selects P of them by P block-wide argmax rounds.
+#include <float.h>
+#include <limits.h>
+#include "internal.cuh"
+
+namespace matcha {
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+            const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+            const T *__restrict__ tw, T *__restrict__ grid) {
+  const int k = blockIdx.x;
+  const long b = blockIdx.y;
+  const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Sg = reinterpret_cast<T *>(smem_raw);  // [W][W] complex, index (m+L0)*W + n+L0
+  T *G = Sg + 2 * W * W;                     // [L0+1][ns] complex
+  const T *cb = c + 4 * b * nc;
+  const T *dk = soft_d + (long)k * nc0;
+  for (int q = threadIdx.x; q < np0; q += blockDim.x) {
+    int m = isqrt_floor(q), n = q - m * m - m;
+    const T *cp = cb + 4L * pair_off[q];
+    const T *dp = dk + pair_off0[q];
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    for (int l = m; l <= L0; ++l) {
+      T d = dp[l - m];
+      const T *e = cp + 4 * (l - m);
+      ar = fma(e[0], d, ar); ai = fma(e[1], d, ai);
+      br = fma(e[2], d, br); bi = fma(e[3], d, bi);
+    }
+    if ((m - n) & 1) { br = -br; bi = -bi; }  // d^l_nm = (-1)^{m-n} d^l_mn
+    auto put = [&](int a, int bb, T re, T im) {
+      int i = (a + L0) * W + (bb + L0);
+      Sg[2 * i] = re; Sg[2 * i + 1] = im;
+    };
+    put(m, n, ar, ai);
+    if (q != 0) put(-m, -n, ar, -ai);
+    if (n != m && n != -m) { put(n, m, br, bi); put(-n, -m, br, -bi); }
+  }
+  __syncthreads();
+  // G_m(j) = sum_n S_mn e^{i n g_j}, m = 0..L0
+  for (int idx = threadIdx.x; idx < (L0 + 1) * ns; idx += blockDim.x) {
+    int m = idx / ns, j = idx - m * ns;
+    T re = 0, im = 0;
+    const T *row = Sg + 2 * (m + L0) * W;
+    for (int n = -L0; n <= L0; ++n) {
+      int t = (int)(((long)n * j) % ns);
+      if (t < 0) t += ns;
+      T cr = tw[2 * t], ci = tw[2 * t + 1];
+      T sr = row[2 * (n + L0)], si = row[2 * (n + L0) + 1];
+      re += sr * cr - si * ci;
+      im += sr * ci + si * cr;
+    }
+    G[2 * idx] = re;
+    G[2 * idx + 1] = im;
+  }
+  __syncthreads();
+  // C(i, k, j) = Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m a_i}
+  T *gb = grid + b * (long)ns * ns * ns;
+  for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
+    int i = idx / ns, j = idx - i * ns;
+    T acc = 0;
+    for (int m = 1; m <= L0; ++m) {
+      int t = (int)(((long)m * i) % ns);
+      T gr = G[2 * (m * ns + j)], gi = G[2 * (m * ns + j) + 1];
+      acc += gr * tw[2 * t] - gi * tw[2 * t + 1];
+    }
+    gb[((long)i * ns + k) * ns + j] = G[2 * j] + 2 * acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool precedes(T va, int ia, T vb, int ib) {
+  return va > vb || (va == vb && ia < ib);
+}
+
+template <typename T>
+__device__ __forceinline__ bool is_local_max(const T *__restrict__ g, int ns, int p) {
+  int i = p / (ns * ns), k = (p / ns) % ns, j = p % ns;
+  T v = g[p];
+  if (v != v) return false;
+  for (int di = -1; di <= 1; ++di) {
+    int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+    for (int dk = -1; dk <= 1; ++dk) {
+      int kk = k + dk;
+      if (kk < 0 || kk >= ns) continue;
+      for (int dj = -1; dj <= 1; ++dj) {
+        if (!di && !dk && !dj) continue;
+        int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+        int q = (ii * ns + kk) * ns + jj;
+        if (!precedes(v, p, g[q], q)) return false;
+      }
+    }
+  }
+  return true;
+}
+
+constexpr int TOPK_CAP = 3072;
+constexpr int TOPK_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(TOPK_THREADS)
+k_topk(const T *__restrict__ grid, int ns, int P_max, const int *__restrict__ P_per,
+       int *__restrict__ idx_out, double *__restrict__ euler_out, double *__restrict__ score_out,
+       int *__restrict__ n_cand_out) {
+  const long b = blockIdx.x;
+  const int tot = ns * ns * ns;
+  const T *g = grid + b * (long)tot;
+  __shared__ int cnt;
+  __shared__ T lv[TOPK_CAP];
+  __shared__ int li[TOPK_CAP];
+  __shared__ T red_v[TOPK_THREADS / 32];
+  __shared__ int red_i[TOPK_THREADS / 32];
+  __shared__ T prev_v;
+  __shared__ int prev_i;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < tot; p += blockDim.x) {
+    if (is_local_max(g, ns, p)) {
+      int pos = atomicAdd(&cnt, 1);
+      if (pos < TOPK_CAP) { lv[pos] = g[p]; li[pos] = p; }
+    }
+  }
+  __syncthreads();
+  const int n_max = cnt;
+  const bool listed = n_max <= TOPK_CAP;
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  const int kept = min(Pb, n_max);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < kept; ++r) {
+    T bv = -INFINITY;
+    int bi = INT_MAX;
+    bool have_prev = r > 0;
+    T pv = have_prev ? prev_v : T(0);
+    int pi = have_prev ? prev_i : 0;
+    if (listed) {
+      for (int t = threadIdx.x; t < n_max; t += blockDim.x) {
+        T v = lv[t];
+        int i = li[t];
+        if (have_prev && !precedes(pv, pi, v, i)) continue;
+        if (bi == INT_MAX || precedes(v, i, bv, bi)) { bv = v; bi = i; }
+      }
+    } else {
+      for (int p = threadIdx.x; p < tot; p += blockDim.x) {
+        T v = g[p];
+        if (have_prev && !precedes(pv, pi, v, p)) continue;
+        if (bi != INT_MAX && !precedes(v, p, bv, bi)) continue;
+        if (!is_local_max(g, ns, p)) continue;
+        bv = v; bi = p;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi != INT_MAX && (bi == INT_MAX || precedes(ov, oi, bv, bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T v = red_v[0];
+      int i = red_i[0];
+      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+        if (red_i[w] != INT_MAX && (i == INT_MAX || precedes(red_v[w], red_i[w], v, i))) {
+          v = red_v[w]; i = red_i[w];
+        }
+      prev_v = v;
+      prev_i = i;
+      long o = b * P_max + r;
+      idx_out[o] = i;
+      score_out[o] = (double)v;
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    }
+    __syncthreads();
+  }
+  for (int r = kept + threadIdx.x; r < P_max; r += blockDim.x) {
+    long o = b * P_max + r;
+    idx_out[o] = -1;
+    score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+    euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+  }
+  if (threadIdx.x == 0) n_cand_out[b] = kept;
+}
+
+template <typename T>
+cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
+                        double *euler, double *score, int *n_cand, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  int W = 2 * p.L0 + 1;
+  size_t smem = sizeof(T) * (2 * (size_t)W * W + 2 * (size_t)(p.L0 + 1) * p.ns);
+  k_soft_grid<T><<<dim3(p.ns, B), 256, smem, st>>>(c, p.nc, p.L0, p.ns, p.pair_off,
+                                                   (const T *)p.soft_d, p.pair_off0, p.nc0,
+                                                   (const T *)p.soft_tw, grid);
+  k_topk<T><<<B, TOPK_THREADS, 0, st>>>(grid, p.ns, p.P, P_per, idx, euler, score, n_cand);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_soft<float>(const Plan &, const float *, int, const int *, float *, int *,
+                                        double *, double *, int *, cudaStream_t);
+template cudaError_t launch_soft<double>(const Plan &, const double *, int, const int *, double *,
+                                         int *, double *, double *, int *, cudaStream_t);
+
+}  // namespace matcha
