@@ -83,6 +83,9 @@ typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1 } matcha_precision;
  *   step_tol     Newton early stop (Section 2.4): a level stops for a candidate
  *                once ||delta||_2 < step_tol (radians); <= 0 selects 1e-9 for
  *                FP64 plans and 1e-6 for FP32 plans.
+ *   accept_tol   a Newton trial is accepted unless it lowers C_L by more than
+ *                accept_tol |C_L|, the rounding level of the Wigner sums;
+ *                <= 0 selects 1e-11 (FP64) or 1e-5 (FP32).
  * The angular sampling is n_theta = L_J + 1 Gauss-Legendre nodes in cos(theta)
  * and n_phi = 2 L_J + 2 equispaced phi per shell. */
 typedef struct {
@@ -97,6 +100,7 @@ typedef struct {
   int L_sched[MATCHA_MAX_LEVELS];
   int precision;
   double step_tol;
+  double accept_tol;
 } matcha_plan_desc;
 
 /* Sizes derived from a plan. */

@@ -26,7 +26,8 @@ class OrcParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("S", ctypes.c_int), ("L0", ctypes.c_int),
                 ("K", ctypes.c_int), ("P", ctypes.c_int), ("M_iter", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("L_sched", ctypes.c_int * 16),
-                ("r_max", ctypes.c_double), ("step_tol", ctypes.c_double)]
+                ("r_max", ctypes.c_double), ("step_tol", ctypes.c_double),
+                ("accept_tol", ctypes.c_double)]
 
 
 def lib():
@@ -255,13 +256,13 @@ def newton_direction(g, H, L):
     return d, fl
 
 
-def newton_march(c, L_sched, M_iter, abg, step_tol=1e-9):
+def newton_march(c, L_sched, M_iter, abg, step_tol=1e-9, accept_tol=1e-11):
     ca = _split(np.asarray(c))
     Ls = np.ascontiguousarray(L_sched, dtype=np.int32)
     x = np.array(abg, dtype=np.float64)
     sc = np.zeros(1)
     fl = lib().orc_newton_march(_d(ca), _i(Ls), ctypes.c_int(len(Ls)), ctypes.c_int(M_iter),
-                                ctypes.c_double(step_tol), _d(x), _d(sc))
+                                ctypes.c_double(step_tol), ctypes.c_double(accept_tol), _d(x), _d(sc))
     return x, sc[0], fl
 
 
@@ -270,7 +271,7 @@ def max_threads():
     return lib().orc_max_threads()
 
 
-def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9):
+def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9, accept_tol=1e-11):
     p = OrcParams()
     p.N, p.S, p.L0, p.K, p.P, p.M_iter = N, S, L0, K, P, M_iter
     p.n_levels = len(L_sched)
@@ -278,11 +279,12 @@ def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9):
         p.L_sched[i] = L
     p.r_max = r_max
     p.step_tol = step_tol
+    p.accept_tol = accept_tol
     return p
 
 
 def align_batch(particles, templates, *, S, r_max, L0, K, P, M_iter, L_sched,
-                P_per=None, n_threads=0, step_tol=1e-9):
+                P_per=None, n_threads=0, step_tol=1e-9, accept_tol=1e-11):
     """Run Algorithm 1 on each (particle, template) pair; returns a dict of arrays.
 
     ``templates`` holds one volume per particle, or a single shared volume.
@@ -291,7 +293,7 @@ def align_batch(particles, templates, *, S, r_max, L0, K, P, M_iter, L_sched,
     temps = np.ascontiguousarray(templates, dtype=np.float32)
     B, N = parts.shape[0], parts.shape[-1]
     tstride = 0 if temps.shape[0] == 1 else N ** 3
-    p = make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol)
+    p = make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol, accept_tol)
     out = dict(euler=np.zeros((B, 3)), R=np.zeros((B, 3, 3)), score=np.zeros(B),
                best_p=np.zeros(B, dtype=np.int32), flags=np.zeros(B, dtype=np.int32),
                cand_idx=np.full((B, P), -1, dtype=np.int32), cand_euler0=np.zeros((B, P, 3)),

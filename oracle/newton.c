@@ -12,8 +12,11 @@
  *      delta = -H^{-1} grad, else delta = grad / ||H||_F  (flag bit 1);
  *   3. clamp ||delta||_2 <= pi / (2 (L_j + 1));
  *   4. trial theta' = wrap(theta + delta); accept when C_{L_j}(theta') >=
- *      C_{L_j}(theta), else halve delta, at most twice; when no trial is
- *      accepted theta stays (flag bit 2);
+ *      C_{L_j}(theta) - accept_tol |C_{L_j}(theta)|, else halve delta, at
+ *      most twice; when no trial is accepted theta stays (flag bit 2).
+ *      accept_tol (1e-11 in double) sits above the rounding level of the
+ *      Wigner sums, so steps near convergence, whose change of C is below
+ *      that level, are not judged on rounding noise;
  *   5. at most M_iter steps per level; the level ends early for a candidate
  *      once ||delta||_2 (after step 2) is below step_tol, the "parameter
  *      increment below a prescribed tolerance" stop of Section 2.4;
@@ -92,7 +95,7 @@ static int finite_all(double C, const double *g, const double *H) {
 /* Refines abg in place through the schedule; *score = C_{L_J}(abg).
  * Returns flag bits. */
 int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_iter,
-                     double step_tol, double *abg, double *score) {
+                     double step_tol, double accept_tol, double *abg, double *score) {
   int flags = 0;
   double C = NAN;
   for (int lev = 0; lev < n_levels; ++lev) {
@@ -108,7 +111,7 @@ int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_it
         double trial[3] = {abg[0] + delta[0], abg[1] + delta[1], abg[2] + delta[2]};
         orc_wrap(trial);
         double Ct = orc_objective(c, L, trial[0], trial[1], trial[2], NULL, NULL, NULL);
-        if (Ct >= C) {
+        if (Ct >= C - accept_tol * fabs(C)) {
           abg[0] = trial[0]; abg[1] = trial[1]; abg[2] = trial[2];
           C = Ct;
           accepted = 1;

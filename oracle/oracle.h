@@ -78,7 +78,7 @@ int  orc_local_maxima_topk(const double *grid, int n, int P, int *idx, double *s
 void orc_wrap(double *abg);
 int  orc_newton_direction(const double *g, const double *H, int L, double *delta);
 int  orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_iter,
-                      double step_tol, double *abg, double *score);
+                      double step_tol, double accept_tol, double *abg, double *score);
 
 /* ---- full path (align.c) ------------------------------------------------ */
 typedef struct {
@@ -86,6 +86,7 @@ typedef struct {
   int L_sched[16];
   double r_max;
   double step_tol;
+  double accept_tol;
 } orc_params;
 
 int orc_align_one(const orc_params *p, const float *particle, const float *tmpl, int P_this,

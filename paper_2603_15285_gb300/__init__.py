@@ -40,7 +40,7 @@ class PlanDesc(ctypes.Structure):
                 ("L0", ctypes.c_int), ("K_oversample", ctypes.c_int), ("P_max", ctypes.c_int),
                 ("M_iter", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("L_sched", ctypes.c_int * MATCHA_MAX_LEVELS), ("precision", ctypes.c_int),
-                ("step_tol", ctypes.c_double)]
+                ("step_tol", ctypes.c_double), ("accept_tol", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -116,7 +116,7 @@ class Plan:
 
     def __init__(self, box_n: int, n_shells: int, L0: int, K: int, P: int, M_iter: int,
                  L_sched: Sequence[int], precision: int = FP64, r_max: float = 0.0,
-                 step_tol: float = 0.0):
+                 step_tol: float = 0.0, accept_tol: float = 0.0):
         _torch()
         d = PlanDesc()
         d.box_n, d.n_shells, d.r_max = box_n, n_shells, r_max
@@ -126,7 +126,7 @@ class Plan:
             raise MatchaError("matcha_plan_create: invalid argument (L_sched length)")
         for k, L in enumerate(L_sched):
             d.L_sched[k] = int(L)
-        d.precision, d.step_tol = precision, step_tol
+        d.precision, d.step_tol, d.accept_tol = precision, step_tol, accept_tol
         h = _vp()
         _check(lib().matcha_plan_create(ctypes.byref(d), ctypes.byref(h)), "matcha_plan_create")
         self._h = h

@@ -12,7 +12,7 @@ struct Plan {
   matcha_plan_desc desc;
   int N, S, LJ, L0, K, P, M, nlev;
   int Ls[MATCHA_MAX_LEVELS];
-  double R, step_tol;
+  double R, step_tol, accept_tol;
   bool fp64;
   int nt, np, nlm, npairs, npairs0, ns;
   long nc;   // (pair, l) entries per particle, l <= L_J

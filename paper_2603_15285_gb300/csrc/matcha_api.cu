@@ -92,7 +92,8 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
     if (d->L_sched[i] <= d->L_sched[i - 1]) return MATCHA_ERR_INVALID_ARG;
   if (d->L_sched[d->n_levels - 1] > MATCHA_MAX_L) return MATCHA_ERR_UNSUPPORTED;
   if (d->precision != MATCHA_FP64 && d->precision != MATCHA_FP32) return MATCHA_ERR_INVALID_ARG;
-  if (!(isfinite(d->r_max)) || !(isfinite(d->step_tol))) return MATCHA_ERR_INVALID_ARG;
+  if (!isfinite(d->r_max) || !isfinite(d->step_tol) || !isfinite(d->accept_tol))
+    return MATCHA_ERR_INVALID_ARG;
 
   Plan *p = new Plan();
   p->desc = *d;
@@ -103,6 +104,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->R = d->r_max > 0 ? d->r_max : 0.5 * d->box_n - 1.0;
   p->fp64 = d->precision == MATCHA_FP64;
   p->step_tol = d->step_tol > 0 ? d->step_tol : (p->fp64 ? 1e-9 : 1e-6);
+  p->accept_tol = d->accept_tol > 0 ? d->accept_tol : (p->fp64 ? 1e-11 : 1e-5);
   p->nt = p->LJ + 1;
   p->np = 2 * p->LJ + 2;
   p->nlm = (p->LJ + 1) * (p->LJ + 2) / 2;

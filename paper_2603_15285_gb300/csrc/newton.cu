@@ -22,7 +22,8 @@
 //   > 1e-12 ||H||_F), else grad / ||H||_F (flag bit 1); ||delta|| clamped to
 //   pi / (2 (L+1)); the level ends early when ||delta|| < step_tol
 //   (Section 2.4); trial theta' = wrap(theta + delta) is accepted when
-//   C(theta') >= C(theta), else delta is halved (at most twice); three
+//   C(theta') >= C(theta) - acc_tol |C(theta)| (acc_tol above the rounding
+//   level of the sums), else delta is halved (at most twice); three
 //   rejected trials end the level for that candidate (flag bit 2), since a
 //   repeated step from the same point would reject again.  Angles, the 3x3
 //   solve and the acceptance test are FP64 in both precisions.
@@ -39,7 +40,7 @@ enum { ST_RUN = 0, ST_TRIAL = 1, ST_STOP = 2, ST_DEAD = 3 };
 struct NewtonArgs {
   int LJ, nlev, M, P, cpw;
   int Ls[MATCHA_MAX_LEVELS];
-  double tol;
+  double tol, acc_tol;
   long nc;
 };
 
@@ -399,7 +400,7 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
         evaluate<T, false>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
         if (tid < P && need[tid]) {
           double Ct = sm.res[10 * tid];
-          if (Ct >= sm.Cc[tid]) {
+          if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
             for (int i = 0; i < 3; ++i) sm.th[3 * tid + i] = sm.tr[3 * tid + i];
             sm.Cc[tid] = Ct;
             sm.state[tid] = ST_RUN;
@@ -456,6 +457,7 @@ cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, d
   A.cpw = cpw;
   for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
   A.tol = p.step_tol;
+  A.acc_tol = p.accept_tol;
   A.nc = p.nc;
   size_t smem = newton_smem_bytes(p, sizeof(T));
   cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
