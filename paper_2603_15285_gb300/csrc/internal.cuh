@@ -20,7 +20,7 @@ struct Plan {
   // device tables (one allocation)
   void *base = nullptr;
   double *rs, *wrad, *xj, *wj;  // S, S, nt, nt (FP64 always)
-  void *ptab;                   // real [nlm][nt]: w_j (2 pi / n_phi) Pbar_lm(x_j)
+  void *ptab;                   // real [nt][nlm]: w_j (2 pi / n_phi) Pbar_lm(x_j)
   void *phi_cs;                 // real [np][2]: cos, sin (2 pi k / n_phi)
   void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout

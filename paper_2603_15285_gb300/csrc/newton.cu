@@ -65,38 +65,66 @@ template <> __device__ __forceinline__ double tsin<double>(double x) { return si
 struct SmemLayout {
   double *th, *tr, *del, *Cc, *res, *red;
   int *state, *steps, *tries, *fl;
-  void *evp, *ea, *eg;
+  void *evp, *ea, *eg, *pw;
+};
+
+// 16-byte (FP32) or 32-byte (FP64) entry of four reals.
+template <typename T> struct Quad;
+template <> struct Quad<float> {
+  float4 v;
+  __device__ __forceinline__ void load(const float *p) { v = __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ __forceinline__ float x() const { return v.x; }
+  __device__ __forceinline__ float y() const { return v.y; }
+  __device__ __forceinline__ float z() const { return v.z; }
+  __device__ __forceinline__ float w() const { return v.w; }
+};
+template <> struct Quad<double> {
+  double2 a, b;
+  __device__ __forceinline__ void load(const double *p) {
+    a = __ldg(reinterpret_cast<const double2 *>(p));
+    b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  }
+  __device__ __forceinline__ double x() const { return a.x; }
+  __device__ __forceinline__ double y() const { return a.y; }
+  __device__ __forceinline__ double z() const { return b.x; }
+  __device__ __forceinline__ double w() const { return b.y; }
 };
 
 // Accumulates the contributions of one order pair for one candidate.
+// pc[k] = cos(b/2)^k and ps[k] = sin(b/2)^k of the candidate (k <= 2L+2).
 template <typename T, bool FULL>
 __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__restrict__ rp, T K,
-                                         int m, int n, int L, T x, T s, T ch, T sh, T *A) {
+                                         int m, int n, int L, T x, T s, const T *pc, const T *ps,
+                                         T *A) {
   // seed at l = m: d = sigma K ch^a sh^b, a = m+n, b = m-n, sigma = (-1)^b
   const int a = m + n, bq = m - n;
-  T c_a = ipow_t(ch, a), s_b = ipow_t(sh, bq);
-  T sg = (bq & 1) ? T(-1) : T(1);
-  T d0 = sg * K * c_a * s_b, d1 = 0, d2 = 0;
+  const T gK = ((bq & 1) ? -K : K);
+  T d0 = gK * pc[a] * ps[bq], d1 = 0, d2 = 0;
   if (FULL) {
-    // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2, and the
-    // second derivative from differentiating once more.
-    T c_am1 = a >= 1 ? ipow_t(ch, a - 1) : T(0);
-    T c_am2 = a >= 2 ? ipow_t(ch, a - 2) : T(0);
-    T s_bm1 = bq >= 1 ? ipow_t(sh, bq - 1) : T(0);
-    T s_bm2 = bq >= 2 ? ipow_t(sh, bq - 2) : T(0);
-    T c_ap1 = c_a * ch, c_ap2 = c_ap1 * ch, s_bp1 = s_b * sh, s_bp2 = s_bp1 * sh;
-    T gK = sg * K;
-    d1 = gK * T(0.5) * (T(bq) * c_ap1 * s_bm1 - T(a) * c_am1 * s_bp1);
-    d2 = gK * T(0.25) *
-         (T(bq * (bq - 1)) * c_ap2 * s_bm2 - T(bq * (a + 1) + a * (bq + 1)) * c_a * s_b +
-          T(a * (a - 1)) * c_am2 * s_bp2);
+    // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2; the
+    // second derivative differentiates once more.  Terms with a zero
+    // coefficient are skipped, so no negative power is read.
+    T t1 = bq >= 1 ? T(bq) * pc[a + 1] * ps[bq - 1] : T(0);
+    T t2 = a >= 1 ? T(a) * pc[a - 1] * ps[bq + 1] : T(0);
+    d1 = gK * T(0.5) * (t1 - t2);
+    T u1 = bq >= 2 ? T(bq * (bq - 1)) * pc[a + 2] * ps[bq - 2] : T(0);
+    T u2 = T(bq * (a + 1) + a * (bq + 1)) * pc[a] * ps[bq];
+    T u3 = a >= 2 ? T(a * (a - 1)) * pc[a - 2] * ps[bq + 2] : T(0);
+    d2 = gK * T(0.25) * (u1 - u2 + u3);
   }
   T p0 = 0, p1 = 0, p2 = 0;  // previous-degree values
   T a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
   T b0r = 0, b0i = 0, b1r = 0, b1i = 0, b2r = 0, b2i = 0;
+  Quad<T> e, r, en, rn;
+  e.load(cp);
+  if (L > m) r.load(rp);
   for (int l = m;; ++l) {
-    const T *e = cp + 4 * (l - m);
-    T cr = e[0], ci = e[1], dr = e[2], di = e[3];
+    const int i = l - m;
+    if (l < L) {  // next degree's entries, one step ahead
+      en.load(cp + 4 * (i + 1));
+      if (l + 1 < L) rn.load(rp + 4 * (i + 1));
+    }
+    T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
     a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
     b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
     if (FULL) {
@@ -106,8 +134,7 @@ __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__re
       b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
     }
     if (l == L) break;
-    const T *r = rp + 4 * (l - m);
-    T ca = r[0], cb = r[1], ce = r[2];
+    T ca = r.x(), cb = r.y(), ce = r.z();
     T t = fma(ca, x, -cb);
     T n0 = fma(t, d0, -ce * p0);
     if (FULL) {
@@ -118,6 +145,8 @@ __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__re
       p2 = d2; d2 = n2;
     }
     p0 = d0; d0 = n0;
+    e = en;
+    r = rn;
   }
   A[0] = a0r; A[1] = a0i; A[2] = b0r; A[3] = b0i;
   if (FULL) {
@@ -155,6 +184,8 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   T *evp = (T *)sm.evp;  // [P][8]: x, s, ch, sh, cos a, sin a, cos g, sin g
   T *ea = (T *)sm.ea;    // [P][W][2]: e^{i m a}, m = -L..L
   T *eg = (T *)sm.eg;
+  T *pw = (T *)sm.pw;    // [P][2][NPW]: ch^k, sh^k
+  const int NPW = 2 * A.LJ + 3;
   const int tid = threadIdx.x;
   if (tid < P && need[tid]) {
     T al = (T)pts[3 * tid], be = (T)pts[3 * tid + 1], ga = (T)pts[3 * tid + 2];
@@ -165,6 +196,11 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
     e[6] = tcos(ga); e[7] = tsin(ga);
   }
   __syncthreads();
+  for (int t = tid; t < 2 * P * (2 * L + 3); t += blockDim.x) {
+    int p = t / (2 * (2 * L + 3)), r = t - p * 2 * (2 * L + 3);
+    int which = r / (2 * L + 3), k = r - which * (2 * L + 3);
+    if (need[p]) pw[(2 * p + which) * NPW + k] = ipow_t(evp[8 * p + 2 + which], k);
+  }
   if (tid < 2 * P) {
     int p = tid >> 1, which = tid & 1;
     if (need[p]) {
@@ -193,14 +229,15 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   for (int i = 0; i < 10; ++i) acc[i] = 0;
   if (act) {
     const T *e = evp + 8 * p;
-    T x = e[0], s = e[1], ch = e[2], sh = e[3];
+    T x = e[0], s = e[1];
     const T *eap = ea + 2 * (long)p * W, *egp = eg + 2 * (long)p * W;
+    const T *pcp = pw + (2 * p) * NPW, *psp = pw + (2 * p + 1) * NPW;
     const int npl = (L + 1) * (L + 1);
     for (int q = slot; q < npl; q += nslots) {
       int m = isqrt_floor(q), n = q - m * m - m;
       int off = pair_off[q];
       T Acc[12];
-      pair_sum<T, FULL>(cb + 4L * off, rcoef + 4L * off, seedK[q], m, n, L, x, s, ch, sh, Acc);
+      pair_sum<T, FULL>(cb + 4L * off, rcoef + 4L * off, seedK[q], m, n, L, x, s, pcp, psp, Acc);
       // image (m, n) and its negation
       {
         T er = eap[2 * (m + L)] * egp[2 * (n + L)] - eap[2 * (m + L) + 1] * egp[2 * (n + L) + 1];
@@ -309,7 +346,7 @@ __device__ int newton_dir(const double *g, const double *H, int L, double *d) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NEWTON_THREADS)
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 2 : 3)
 k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__restrict__ rcoef,
          const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
          double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
@@ -338,6 +375,7 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   sm.evp = tp; tp += 8 * P;
   sm.ea = tp; tp += 2 * P * Wm;
   sm.eg = tp; tp += 2 * P * Wm;
+  sm.pw = tp; tp += 2 * P * (2 * A.LJ + 3);
 
   const int nc_b = n_cand[b];
   if (tid < P) {
@@ -442,7 +480,7 @@ size_t newton_smem_bytes(const Plan &p, size_t tsize) {
   size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
-  bytes += tsize * (8 * P + 4 * P * W);
+  bytes += tsize * (8 * P + 4 * P * W + 2 * P * (2 * (size_t)p.LJ + 3));
   return bytes;
 }
 

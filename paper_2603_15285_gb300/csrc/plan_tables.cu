@@ -62,12 +62,12 @@ __device__ double plm_bar_dev(int l, int m, double x) {
   return pb;
 }
 
-// ptab[lm][j] = w_j (2 pi / n_phi) Pbar_lm(x_j)
+// ptab[j][lm] = w_j (2 pi / n_phi) Pbar_lm(x_j)  (lm fastest)
 __global__ void k_ptab(int L, int nt, int np, const double *xj, const double *wj, double *pt) {
   int nlm = (L + 1) * (L + 2) / 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nlm * nt) return;
-  int lm = t / nt, j = t - lm * nt;
+  int j = t / nlm, lm = t - j * nlm;
   int l = 0;
   while ((l + 1) * (l + 2) / 2 <= lm) ++l;
   int m = lm - l * (l + 1) / 2;

@@ -200,10 +200,227 @@ k_topk(const T *__restrict__ grid, int ns, int P_max, const int *__restrict__ P_
   if (threadIdx.x == 0) n_cand_out[b] = kept;
 }
 
+// Fused variant for grids that fit in shared memory (FP32, n^3 * 4 bytes plus
+// work space <= 227 KB): one CTA per particle computes the grid slice by slice
+// (KB beta values at a time) into shared memory, optionally copies it out,
+// tests local maxima against shared memory (face neighbours first, the
+// cheapest rejection) and selects the top P like k_topk.
+constexpr int FUSED_THREADS = 1024;
+constexpr int FUSED_KB = 4;
+
+__device__ __forceinline__ bool is_local_max_smem(const float *g, int ns, int p) {
+  int i = p / (ns * ns), k = (p / ns) % ns, j = p % ns;
+  float v = g[p];
+  if (v != v) return false;
+  int im = i == 0 ? ns - 1 : i - 1, ip = i == ns - 1 ? 0 : i + 1;
+  int jm = j == 0 ? ns - 1 : j - 1, jp = j == ns - 1 ? 0 : j + 1;
+  // face neighbours first
+  {
+    int q;
+    q = (im * ns + k) * ns + j; if (!precedes(v, p, g[q], q)) return false;
+    q = (ip * ns + k) * ns + j; if (!precedes(v, p, g[q], q)) return false;
+    q = (i * ns + k) * ns + jm; if (!precedes(v, p, g[q], q)) return false;
+    q = (i * ns + k) * ns + jp; if (!precedes(v, p, g[q], q)) return false;
+    if (k > 0) { q = (i * ns + k - 1) * ns + j; if (!precedes(v, p, g[q], q)) return false; }
+    if (k < ns - 1) { q = (i * ns + k + 1) * ns + j; if (!precedes(v, p, g[q], q)) return false; }
+  }
+  const int is[3] = {im, i, ip}, js[3] = {jm, j, jp};
+  for (int a = 0; a < 3; ++a)
+    for (int dk = -1; dk <= 1; ++dk) {
+      int kk = k + dk;
+      if (kk < 0 || kk >= ns) continue;
+      for (int c = 0; c < 3; ++c) {
+        int nz = (a != 1) + (dk != 0) + (c != 1);
+        if (nz < 2) continue;  // the centre and the face neighbours are done
+        int q = (is[a] * ns + kk) * ns + js[c];
+        if (!precedes(v, p, g[q], q)) return false;
+      }
+    }
+  return true;
+}
+
+__global__ void __launch_bounds__(FUSED_THREADS)
+k_soft_fused(const float *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+             const float *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+             const float *__restrict__ tw, int P_max, const int *__restrict__ P_per,
+             float *__restrict__ grid_out, int *__restrict__ idx_out,
+             double *__restrict__ euler_out, double *__restrict__ score_out,
+             int *__restrict__ n_cand_out) {
+  const long b = blockIdx.x;
+  const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1), tot = ns * ns * ns;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *g = reinterpret_cast<float *>(smem_raw);          // [ns^3]
+  float *Sg = g + tot;                                       // [KB][W*W] complex
+  float *G = Sg + 2 * FUSED_KB * W * W;                      // [KB][(L0+1)*ns] complex
+  const float *cb = c + 4 * b * nc;
+  for (int k0 = 0; k0 < ns; k0 += FUSED_KB) {
+    for (int t = tid; t < FUSED_KB * np0; t += NT) {
+      int kk = t / np0, q = t - kk * np0, k = k0 + kk;
+      if (k >= ns) continue;
+      int m = isqrt_floor(q), n = q - m * m - m;
+      const float *cp = cb + 4L * pair_off[q];
+      const float *dp = soft_d + (long)k * nc0 + pair_off0[q];
+      float ar = 0, ai = 0, br = 0, bi = 0;
+      for (int l = m; l <= L0; ++l) {
+        float d = dp[l - m];
+        const float *e = cp + 4 * (l - m);
+        ar = fmaf(e[0], d, ar); ai = fmaf(e[1], d, ai);
+        br = fmaf(e[2], d, br); bi = fmaf(e[3], d, bi);
+      }
+      if ((m - n) & 1) { br = -br; bi = -bi; }
+      float *S = Sg + 2 * kk * W * W;
+      int i0 = (m + L0) * W + (n + L0);
+      S[2 * i0] = ar; S[2 * i0 + 1] = ai;
+      if (q != 0) { int i1 = (-m + L0) * W + (-n + L0); S[2 * i1] = ar; S[2 * i1 + 1] = -ai; }
+      if (n != m && n != -m) {
+        int i2 = (n + L0) * W + (m + L0), i3 = (-n + L0) * W + (-m + L0);
+        S[2 * i2] = br; S[2 * i2 + 1] = bi;
+        S[2 * i3] = br; S[2 * i3 + 1] = -bi;
+      }
+    }
+    __syncthreads();
+    const int nG = (L0 + 1) * ns;
+    for (int t = tid; t < FUSED_KB * nG; t += NT) {
+      int kk = t / nG, r = t - kk * nG;
+      if (k0 + kk >= ns) continue;
+      int m = r / ns, j = r - m * ns;
+      const float *row = Sg + 2 * kk * W * W + 2 * (m + L0) * W;
+      float re = 0, im = 0;
+      int tt = (int)(((long)(-L0) * j) % ns);
+      if (tt < 0) tt += ns;
+      for (int n = -L0; n <= L0; ++n) {
+        float cr = tw[2 * tt], ci = tw[2 * tt + 1];
+        float sr = row[2 * (n + L0)], si = row[2 * (n + L0) + 1];
+        re += sr * cr - si * ci;
+        im += sr * ci + si * cr;
+        tt += j; if (tt >= ns) tt -= ns;
+      }
+      float *Gk = G + 2 * kk * nG;
+      Gk[2 * r] = re; Gk[2 * r + 1] = im;
+    }
+    __syncthreads();
+    for (int t = tid; t < FUSED_KB * ns * ns; t += NT) {
+      int kk = t / (ns * ns), r = t - kk * ns * ns, k = k0 + kk;
+      if (k >= ns) continue;
+      int i = r / ns, j = r - i * ns;
+      const float *Gk = G + 2 * kk * nG;
+      float acc = 0;
+      int tt = i;
+      for (int m = 1; m <= L0; ++m) {
+        float gr = Gk[2 * (m * ns + j)], gi = Gk[2 * (m * ns + j) + 1];
+        acc += gr * tw[2 * tt] - gi * tw[2 * tt + 1];
+        tt += i; if (tt >= ns) tt -= ns;
+      }
+      g[((long)i * ns + k) * ns + j] = Gk[2 * j] + 2 * acc;
+    }
+    __syncthreads();
+  }
+  if (grid_out) {
+    float *go = grid_out + b * (long)tot;
+    for (int t = tid; t < tot; t += NT) go[t] = g[t];
+  }
+  // candidates: reuse the work space after the grid
+  __shared__ int cnt;
+  __shared__ float red_v[FUSED_THREADS / 32];
+  __shared__ int red_i[FUSED_THREADS / 32];
+  __shared__ float prev_v;
+  __shared__ int prev_i;
+  float *lv = Sg;
+  int *li = reinterpret_cast<int *>(Sg) + (FUSED_KB * W * W + FUSED_KB * (L0 + 1) * ns);
+  const int cap = FUSED_KB * W * W + FUSED_KB * (L0 + 1) * ns;  // entries of each array
+  if (tid == 0) cnt = 0;
+  __syncthreads();
+  for (int p = tid; p < tot; p += NT) {
+    if (is_local_max_smem(g, ns, p)) {
+      int pos = atomicAdd(&cnt, 1);
+      if (pos < cap) { lv[pos] = g[p]; li[pos] = p; }
+    }
+  }
+  __syncthreads();
+  const int n_max = cnt;
+  const bool listed = n_max <= cap;
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  const int kept = min(Pb, n_max);
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int r = 0; r < kept; ++r) {
+    float bv = -INFINITY;
+    int bi = INT_MAX;
+    bool have_prev = r > 0;
+    float pv = have_prev ? prev_v : 0.f;
+    int pi = have_prev ? prev_i : 0;
+    if (listed) {
+      for (int t = tid; t < n_max; t += NT) {
+        float v = lv[t];
+        int i = li[t];
+        if (have_prev && !precedes(pv, pi, v, i)) continue;
+        if (bi == INT_MAX || precedes(v, i, bv, bi)) { bv = v; bi = i; }
+      }
+    } else {
+      for (int p = tid; p < tot; p += NT) {
+        float v = g[p];
+        if (have_prev && !precedes(pv, pi, v, p)) continue;
+        if (bi != INT_MAX && !precedes(v, p, bv, bi)) continue;
+        if (!is_local_max_smem(g, ns, p)) continue;
+        bv = v; bi = p;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi != INT_MAX && (bi == INT_MAX || precedes(ov, oi, bv, bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float v = red_v[0];
+      int i = red_i[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (red_i[w] != INT_MAX && (i == INT_MAX || precedes(red_v[w], red_i[w], v, i))) {
+          v = red_v[w]; i = red_i[w];
+        }
+      prev_v = v;
+      prev_i = i;
+      long o = b * P_max + r;
+      idx_out[o] = i;
+      score_out[o] = (double)v;
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    }
+    __syncthreads();
+  }
+  for (int r = kept + tid; r < P_max; r += NT) {
+    long o = b * P_max + r;
+    idx_out[o] = -1;
+    score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+    euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+  }
+  if (tid == 0) n_cand_out[b] = kept;
+}
+
+size_t soft_fused_smem(const Plan &p) {
+  int W = 2 * p.L0 + 1;
+  size_t tot = (size_t)p.ns * p.ns * p.ns;
+  return sizeof(float) * (tot + 2 * (size_t)FUSED_KB * W * W + 2 * (size_t)FUSED_KB * (p.L0 + 1) * p.ns);
+}
+
+bool soft_fused_ok(const Plan &p) { return !p.fp64 && soft_fused_smem(p) <= 227 * 1024 - 1024; }
+
 template <typename T>
 cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
                         double *euler, double *score, int *n_cand, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  if (sizeof(T) == 4 && soft_fused_ok(p)) {
+    size_t smem = soft_fused_smem(p);
+    cudaFuncSetAttribute(k_soft_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_soft_fused<<<B, FUSED_THREADS, smem, st>>>(
+        (const float *)c, p.nc, p.L0, p.ns, p.pair_off, (const float *)p.soft_d, p.pair_off0,
+        p.nc0, (const float *)p.soft_tw, p.P, P_per, (float *)grid, idx, euler, score, n_cand);
+    return cudaGetLastError();
+  }
   int W = 2 * p.L0 + 1;
   size_t smem = sizeof(T) * (2 * (size_t)W * W + 2 * (size_t)(p.L0 + 1) * p.ns);
   k_soft_grid<T><<<dim3(p.ns, B), 256, smem, st>>>(c, p.nc, p.L0, p.ns, p.pair_off,

@@ -108,100 +108,127 @@ def blob_params(rng: np.random.Generator, n_blobs: int, ball_radius: float):
     return np.array(cs), amps
 
 
-def render_blobs(N: int, offsets: np.ndarray, amps: np.ndarray, sigma: float,
-                 device="cpu") -> torch.Tensor:
-    """Sum of isotropic Gaussians at voxel centres; returns float64 [z][y][x].
+def render_blobs(N: int, offsets, amps, sigma: float, device="cpu") -> torch.Tensor:
+    """Sum of isotropic Gaussians at voxel centres; float64 [z][y][x].
 
-    An isotropic Gaussian factorises over x, y, z, so the volume is a sum of
-    outer products of three 1-D profiles.
+    ``offsets`` [n][3] (x, y, z relative to N/2) and ``amps`` [n], or batched
+    [B][n][3] and [B][n] for a [B][z][y][x] result.  An isotropic Gaussian
+    factorises over x, y, z, so each volume is a sum of outer products of
+    three 1-D profiles.
     """
     c0 = N / 2
     grid = torch.arange(N, dtype=torch.float64, device=device) - c0
     off = torch.as_tensor(offsets, dtype=torch.float64, device=device)
     a = torch.as_tensor(amps, dtype=torch.float64, device=device)
-    g = torch.exp(-(grid[None, None, :] - off[:, :, None]) ** 2 / (2 * sigma * sigma))  # [b][xyz][N]
-    return torch.einsum("b,bz,by,bx->zyx", a, g[:, 2], g[:, 1], g[:, 0])
+    batched = off.dim() == 3
+    if not batched:
+        off, a = off[None], a[None]
+    g = torch.exp(-(grid[None, None, None, :] - off[..., None]) ** 2 / (2 * sigma * sigma))  # [B][n][xyz][N]
+    v = torch.einsum("cb,cbz,cby,cbx->czyx", a, g[:, :, 2], g[:, :, 1], g[:, :, 0])
+    return v if batched else v[0]
 
 
-def rotate_trilinear(vol: torch.Tensor, R: np.ndarray) -> torch.Tensor:
-    """out(x) = vol(R^T (x - c0) + c0) by trilinear interpolation, zero outside."""
-    N = vol.shape[-1]
+def rotate_trilinear(vol: torch.Tensor, R) -> torch.Tensor:
+    """out(x) = vol(R^T (x - c0) + c0) by trilinear interpolation, zero outside.
+
+    ``vol`` [N][N][N] with R [3][3], or batched [B][N][N][N] with R [B][3][3].
+    """
+    batched = vol.dim() == 4
+    if not batched:
+        vol, R = vol[None], np.asarray(R)[None]
+    Bn, N = vol.shape[0], vol.shape[-1]
     dev = vol.device
     c0 = N / 2
-    Rt = torch.as_tensor(R, dtype=torch.float64, device=dev).T
+    Rt = torch.as_tensor(np.asarray(R), dtype=torch.float64, device=dev)   # [B][3][3]
     ax = torch.arange(N, dtype=torch.float64, device=dev) - c0
     zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
-    pts = torch.stack([xx, yy, zz], -1).reshape(-1, 3) @ Rt.T + c0   # (x, y, z)
+    x = torch.stack([xx, yy, zz], -1).reshape(-1, 3)                          # [V][3]
+    pts = torch.einsum("vj,bij->bvi", x, Rt.transpose(1, 2)) + c0             # R^T x + c0
     i0 = torch.floor(pts).long()
     fr = pts - i0
-    out = torch.zeros(pts.shape[0], dtype=vol.dtype, device=dev)
-    flat = vol.reshape(-1)
+    out = torch.zeros(pts.shape[:2], dtype=vol.dtype, device=dev)
+    flat = vol.reshape(Bn, -1)
     for dz in (0, 1):
         for dy in (0, 1):
             for dx in (0, 1):
-                ix, iy, iz = i0[:, 0] + dx, i0[:, 1] + dy, i0[:, 2] + dz
-                w = ((fr[:, 0] if dx else 1 - fr[:, 0]) * (fr[:, 1] if dy else 1 - fr[:, 1])
-                     * (fr[:, 2] if dz else 1 - fr[:, 2]))
+                ix, iy, iz = i0[..., 0] + dx, i0[..., 1] + dy, i0[..., 2] + dz
+                w = ((fr[..., 0] if dx else 1 - fr[..., 0]) * (fr[..., 1] if dy else 1 - fr[..., 1])
+                     * (fr[..., 2] if dz else 1 - fr[..., 2]))
                 ok = (ix >= 0) & (ix < N) & (iy >= 0) & (iy < N) & (iz >= 0) & (iz < N)
                 lin = (iz.clamp(0, N - 1) * N + iy.clamp(0, N - 1)) * N + ix.clamp(0, N - 1)
-                out += torch.where(ok, w * flat[lin], torch.zeros_like(w))
-    return out.reshape(N, N, N)
+                out += torch.where(ok, w * torch.gather(flat, 1, lin), torch.zeros_like(w))
+    out = out.reshape(Bn, N, N, N)
+    return out if batched else out[0]
 
 
 def apply_missing_wedge(vol: torch.Tensor, wedge_deg: float) -> torch.Tensor:
-    """Zero the Fourier samples outside a +-wedge_deg tilt range (axis y, beam z)."""
+    """Zero the Fourier samples outside a +-wedge_deg tilt range (axis y, beam z).
+
+    Acts on the last three axes, so batches of volumes work unchanged.
+    """
     N = vol.shape[-1]
-    F = torch.fft.fftn(vol)
+    F = torch.fft.fftn(vol, dim=(-3, -2, -1))
     k = torch.fft.fftfreq(N, device=vol.device, dtype=torch.float64)
     kz, ky, kx = torch.meshgrid(k, k, k, indexing="ij")
     keep = kz.abs() <= math.tan(math.radians(wedge_deg)) * kx.abs() + 1e-12
     keep |= (kz == 0) & (kx == 0) & (ky == 0)
-    return torch.fft.ifftn(F * keep).real
+    return torch.fft.ifftn(F * keep, dim=(-3, -2, -1)).real
 
 
 def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu",
-               exact_rotation: bool = False, noise: bool = True):
+               exact_rotation: bool = False, noise: bool = True, chunk: int = 64):
     """Generate particles ``start .. start+B-1`` of workload ``w``.
 
     Returns dict with ``templates`` (float32 [Bt][N][N][N], Bt = 1 when the
     workload shares one template, else B), ``particles`` (float32 [B][N][N][N]),
-    ``R_true`` (float64 [B][3][3]).
+    ``R_true`` (float64 [B][3][3]).  Random draws are made per particle on the
+    host; rendering runs in chunks of ``chunk`` particles on ``device``.
     """
     B = w.B if B is None else B
     seeds = np.random.SeedSequence(w.base_seed).spawn(start + B)[start:]
     N = w.N
     parts = torch.empty((B, N, N, N), dtype=torch.float32, device=device)
-    temps = []
+    temps = None if w.shared_template else torch.empty((B, N, N, N), dtype=torch.float32, device=device)
     Rs = np.empty((B, 3, 3))
     shared = None
     if w.shared_template:
         trng = np.random.default_rng(np.random.SeedSequence(w.base_seed + 7919))
         offs, amps = blob_params(trng, w.n_blobs, w.ball_radius)
         shared = (offs, amps, render_blobs(N, offs, amps, w.sigma, device))
-        temps.append(shared[2].float())
-    for b, ss in enumerate(seeds):
-        rng = np.random.default_rng(ss)
+        temps = shared[2].float()[None].contiguous()
+    for c0 in range(0, B, chunk):
+        idx = range(c0, min(B, c0 + chunk))
+        offs_l, amps_l, etas = [], [], []
+        for b in idx:
+            rng = np.random.default_rng(seeds[b])
+            if shared is None:
+                offs, amps = blob_params(rng, w.n_blobs, w.ball_radius)
+            else:
+                offs, amps = shared[0], shared[1]
+            offs_l.append(offs); amps_l.append(amps)
+            Rs[b] = haar_rotation(rng)
+            if noise and w.snr is not None and w.snr > 0:
+                etas.append(rng.standard_normal((N, N, N), dtype=np.float32))
+        Rc = Rs[c0:c0 + len(idx)]
         if shared is None:
-            offs, amps = blob_params(rng, w.n_blobs, w.ball_radius)
-            h = render_blobs(N, offs, amps, w.sigma, device)
-            temps.append(h.float())
+            h = render_blobs(N, np.stack(offs_l), np.stack(amps_l), w.sigma, device)
+            temps[c0:c0 + len(idx)] = h.float()
         else:
-            offs, amps, h = shared
-        R = haar_rotation(rng)
-        Rs[b] = R
+            h = shared[2][None].expand(len(idx), N, N, N)
         if exact_rotation:
-            s = render_blobs(N, offs @ R.T, amps, w.sigma, device)
+            rot = np.einsum("bnj,bij->bni", np.stack(offs_l), Rc)
+            s = render_blobs(N, rot, np.stack(amps_l), w.sigma, device)
         else:
-            s = rotate_trilinear(h, R)
-        if noise and w.snr is not None and w.snr > 0:
-            var = float((s * s).mean()) / w.snr
-            eta = rng.standard_normal((N, N, N), dtype=np.float32)
-            s = s + math.sqrt(var) * torch.from_numpy(eta).to(device=device, dtype=s.dtype)
+            s = rotate_trilinear(h.contiguous(), Rc)
+        if etas:
+            var = (s * s).mean(dim=(1, 2, 3)) / w.snr
+            eta = torch.from_numpy(np.stack(etas)).to(device=device, dtype=s.dtype)
+            s = s + var.sqrt()[:, None, None, None] * eta
         if w.wedge_deg is not None:
             s = apply_missing_wedge(s, w.wedge_deg)
-        parts[b] = s.float()
+        parts[c0:c0 + len(idx)] = s.float()
     return {
-        "templates": torch.stack(temps),
+        "templates": temps,
         "particles": parts,
         "R_true": Rs,
     }

@@ -198,3 +198,43 @@ def test_host_buffers_match_device_path():
     host = m.matcha_align_host(plan, d["particles"].numpy(), d["templates"].numpy())
     assert np.array_equal(host["R"], dev["R"].cpu().numpy())
     assert np.array_equal(host["score"], dev["score"].cpu().numpy())
+
+
+def _brute_top_p(grid, n, P):
+    """Local maxima in (value desc, index asc) order, decided in grid's own dtype."""
+    g = grid.reshape(n, n, n)
+    out = []
+    for i in range(n):
+        for k in range(n):
+            for j in range(n):
+                p = (i * n + k) * n + j
+                v = g[i, k, j]
+                ok = not np.isnan(v)
+                for di in (-1, 0, 1):
+                    for dk in (-1, 0, 1):
+                        for dj in (-1, 0, 1):
+                            if not ok or (di, dk, dj) == (0, 0, 0) or not 0 <= k + dk < n:
+                                continue
+                            q = (((i + di) % n) * n + k + dk) * n + (j + dj) % n
+                            wv = grid[q]
+                            ok = v > wv or (v == wv and p < q)
+                if ok:
+                    out.append((-float(v), p))
+    out.sort()
+    return [p for _, p in out[:P]]
+
+
+@pytest.mark.parametrize("w", [SMALL, RAGGED], ids=lambda w: w.name)
+def test_soft_grid_and_top_p_fp32(w):
+    d, parts, temps = gen(w)
+    plan = m.plan_for_workload(w, precision=m.FP32)
+    c = m.matcha_correlate_coeffs(plan, m.matcha_analyze(plan, parts), m.matcha_analyze(plan, temps), 1)
+    s = m.matcha_soft_search(plan, c)
+    n = plan.info.soft_n
+    for b in range(parts.shape[0]):
+        cref = corr_to_oracle(c[b].double(), w.L_final)
+        gref = O.soft_grid(cref, w.L0, w.K)
+        ggot = s["grid"][b].cpu().numpy().ravel()
+        assert np.abs(ggot - gref).max() <= 1e-5 * np.abs(gref).max()
+        nc = int(s["n_cand"][b])
+        assert list(s["idx"][b, :nc].cpu().numpy()) == _brute_top_p(ggot, n, w.P)
