@@ -156,6 +156,30 @@ matcha_status matcha_soft_search(matcha_plan plan, const void *c_dev, int B, con
                                  void *grid_dev, int *idx_dev, double *euler_dev,
                                  double *score_dev, int *n_cand_dev, void *stream);
 
+/* matcha_soft_search without caller-provided scratch.  The paper has no
+ * counterpart: this is a library convenience.  It exists for callers that may
+ * not allocate device memory themselves: applications whose device memory is
+ * owned by a single allocator (a framework's caching allocator or a pool sized
+ * at start-up) and latency-critical loops that cannot afford cudaMalloc and
+ * cudaFree, which may synchronise the device.  The caller passes c and the
+ * candidate outputs exactly as for matcha_soft_search; the SOFFT grid lives in
+ * a fixed array of MATCHA_NOALLOC_GRID_BYTES (64 MiB) compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  B * soft_n^3 * real_bytes must fit in it (for the 1024-particle
+ * 64^3 plan with L0 = 8, K = 2: 359 particles per call in FP32, 179 in
+ * FP64); larger batches return MATCHA_ERR_UNSUPPORTED with the limit in
+ * matcha_last_error().  The call allocates nothing.  Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (e.g. on different streams) race on it and must be ordered by the
+ * caller.  The grid is fully rewritten on each call, so leftover contents of
+ * the previous call do not matter. */
+#define MATCHA_NOALLOC_GRID_BYTES (64u << 20)
+matcha_status matcha_soft_search_noalloc(matcha_plan plan, const void *c_dev, int B,
+                                         const int *P_per_dev, int *idx_dev, double *euler_dev,
+                                         double *score_dev, int *n_cand_dev, void *stream);
+
 /* a6: frequency-marched Newton refinement of every candidate (Sections
  * 2.2-2.4, Algorithm 1).  euler_dev is read as the start points and
  * overwritten by the refined angles; score_dev receives C_{L_J} at the

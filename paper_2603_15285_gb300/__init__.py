@@ -28,6 +28,7 @@ SYMBOLS = [
     "matcha_workspace_size", "matcha_analyze", "matcha_correlate_coeffs", "matcha_soft_search",
     "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
+    "matcha_soft_search_noalloc",
 ]
 
 
@@ -70,6 +71,7 @@ def lib():
             "matcha_analyze": [_vp, _vp, i, _vp, _vp],
             "matcha_correlate_coeffs": [_vp, _vp, _vp, i, i, _vp, _vp],
             "matcha_soft_search": [_vp, _vp, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+            "matcha_soft_search_noalloc": [_vp, _vp, i, _vp, _vp, _vp, _vp, _vp, _vp],
             "matcha_newton_march": [_vp, _vp, i, _vp, _vp, _vp, _vp, _vp, _vp],
             "matcha_final_select": [_vp, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
             "matcha_align": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
@@ -223,6 +225,25 @@ def matcha_soft_search(plan: Plan, c, P_per=None, grid=None):
                                     _ptr(euler), _ptr(score), _ptr(ncand), _stream()),
            "matcha_soft_search")
     return dict(grid=grid, idx=idx, euler=euler, score=score, n_cand=ncand)
+
+
+def matcha_soft_search_noalloc(plan: Plan, c, idx, euler, score, n_cand, P_per=None):
+    """matcha_soft_search with the grid in the library's built-in device array.
+
+    For callers that must not allocate device memory: all outputs are passed
+    in (preallocated by the caller), and this call allocates nothing.
+    """
+    torch = _torch()
+    _need(c, plan.real_dtype, "c")
+    _need(idx, torch.int32, "idx"); _need(euler, torch.float64, "euler")
+    _need(score, torch.float64, "score"); _need(n_cand, torch.int32, "n_cand")
+    if P_per is not None:
+        _need(P_per, torch.int32, "P_per")
+    B = c.shape[0]
+    _check(lib().matcha_soft_search_noalloc(plan.handle, _ptr(c), B, _ptr(P_per), _ptr(idx),
+                                            _ptr(euler), _ptr(score), _ptr(n_cand), _stream()),
+           "matcha_soft_search_noalloc")
+    return dict(idx=idx, euler=euler, score=score, n_cand=n_cand)
 
 
 def matcha_newton_march(plan: Plan, c, n_cand, euler, work=None, score=None, flags=None):

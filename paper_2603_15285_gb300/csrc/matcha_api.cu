@@ -64,6 +64,11 @@ bool valid_stride(int s) { return s == 0 || s == 1; }
 
 }  // namespace
 
+namespace matcha {
+// Sets the text matcha_last_error() returns on this thread.
+void set_error_text(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace matcha
+
 extern "C" {
 
 const char *matcha_status_string(matcha_status s) {
