@@ -25,7 +25,7 @@ struct Plan {
   void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
   void *rcoef;                  // real [nc][4]: (a, b, e, 0) of the step l -> l+1
-  void *seedK;                  // real [npairs]: sqrt(binom(2m, m+n))
+  void *seedK;                  // real [npairs][4]: (sqrt(binom(2m, m+n)), 0, 0, 0)
   int *pair_off;                // [npairs] entry offset of pair q in the L_J layout
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 layout
   // host copies of the layout

@@ -130,7 +130,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   auto add = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes); return o; };
   size_t o_rs = add(8 * p->S), o_w = add(8 * p->S), o_x = add(8 * p->nt), o_wj = add(8 * p->nt);
   size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
-  size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * p->npairs);
+  size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->npairs);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
   cudaError_t e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }

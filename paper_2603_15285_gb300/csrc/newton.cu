@@ -65,14 +65,31 @@ template <> __device__ __forceinline__ double tsin<double>(double x) { return si
 struct SmemLayout {
   double *th, *tr, *del, *Cc, *res, *red;
   int *state, *steps, *tries, *fl;
-  void *evp, *ea, *eg, *pw;
+  void *evp, *ea, *eg, *pw, *stage;
 };
+
+// Asynchronous global -> shared copies (no registers involved).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Copies one entry of four reals (16 B in FP32, 32 B in FP64).
+template <typename T>
+__device__ __forceinline__ void copy_quad(T *dst, const T *src) {
+  cp_async16(dst, src);
+  if (sizeof(T) == 8) cp_async16(dst + 2, src + 2);
+}
 
 // 16-byte (FP32) or 32-byte (FP64) entry of four reals.
 template <typename T> struct Quad;
 template <> struct Quad<float> {
   float4 v;
-  __device__ __forceinline__ void load(const float *p) { v = __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ __forceinline__ void load(const float *p) { v = *reinterpret_cast<const float4 *>(p); }
   __device__ __forceinline__ float x() const { return v.x; }
   __device__ __forceinline__ float y() const { return v.y; }
   __device__ __forceinline__ float z() const { return v.z; }
@@ -81,8 +98,8 @@ template <> struct Quad<float> {
 template <> struct Quad<double> {
   double2 a, b;
   __device__ __forceinline__ void load(const double *p) {
-    a = __ldg(reinterpret_cast<const double2 *>(p));
-    b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    a = *reinterpret_cast<const double2 *>(p);
+    b = *(reinterpret_cast<const double2 *>(p) + 1);
   }
   __device__ __forceinline__ double x() const { return a.x; }
   __device__ __forceinline__ double y() const { return a.y; }
@@ -91,11 +108,12 @@ template <> struct Quad<double> {
 };
 
 // Accumulates the contributions of one order pair for one candidate.
-// pc[k] = cos(b/2)^k and ps[k] = sin(b/2)^k of the candidate (k <= 2L+2).
+// st: the pair's entries staged in shared memory, entry i = degree m+i holds
+// (c^l_mn, c^l_nm) in reals 8i..8i+3 and its recurrence coefficients in
+// 8i+4..8i+7.  pc[k] = cos(b/2)^k, ps[k] = sin(b/2)^k of the candidate.
 template <typename T, bool FULL>
-__device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__restrict__ rp, T K,
-                                         int m, int n, int L, T x, T s, const T *pc, const T *ps,
-                                         T *A) {
+__device__ __forceinline__ void pair_sum(const T *st, T K, int m, int n, int L, T x, T s,
+                                         const T *pc, const T *ps, T *A) {
   // seed at l = m: d = sigma K ch^a sh^b, a = m+n, b = m-n, sigma = (-1)^b
   const int a = m + n, bq = m - n;
   const T gK = ((bq & 1) ? -K : K);
@@ -115,15 +133,12 @@ __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__re
   T p0 = 0, p1 = 0, p2 = 0;  // previous-degree values
   T a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
   T b0r = 0, b0i = 0, b1r = 0, b1i = 0, b2r = 0, b2i = 0;
-  Quad<T> e, r, en, rn;
-  e.load(cp);
-  if (L > m) r.load(rp);
-  for (int l = m;; ++l) {
-    const int i = l - m;
-    if (l < L) {  // next degree's entries, one step ahead
-      en.load(cp + 4 * (i + 1));
-      if (l + 1 < L) rn.load(rp + 4 * (i + 1));
-    }
+  const int last = L - m;  // entries 0..last; the recurrence runs for 0..last-1
+#pragma unroll 2
+  for (int i = 0; i < last; ++i) {
+    Quad<T> e, r;
+    e.load(st + 8 * i);
+    r.load(st + 8 * i + 4);
     T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
     a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
     b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
@@ -133,7 +148,6 @@ __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__re
       a2r = fma(cr, d2, a2r); a2i = fma(ci, d2, a2i);
       b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
     }
-    if (l == L) break;
     T ca = r.x(), cb = r.y(), ce = r.z();
     T t = fma(ca, x, -cb);
     T n0 = fma(t, d0, -ce * p0);
@@ -145,8 +159,19 @@ __device__ __forceinline__ void pair_sum(const T *__restrict__ cp, const T *__re
       p2 = d2; d2 = n2;
     }
     p0 = d0; d0 = n0;
-    e = en;
-    r = rn;
+  }
+  {
+    Quad<T> e;
+    e.load(st + 8 * last);
+    T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
+    a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
+    b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
+    if (FULL) {
+      a1r = fma(cr, d1, a1r); a1i = fma(ci, d1, a1i);
+      b1r = fma(dr, d1, b1r); b1i = fma(di, d1, b1i);
+      a2r = fma(cr, d2, a2r); a2i = fma(ci, d2, a2i);
+      b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
+    }
   }
   A[0] = a0r; A[1] = a0i; A[2] = b0r; A[3] = b0i;
   if (FULL) {
@@ -221,23 +246,46 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   const int lane = tid & 31, warp = tid >> 5;
   const int spw = 32 / cpw;
   const int p = lane & (cpw - 1);
-  const int slot = warp * spw + lane / cpw;
+  const int sub = lane / cpw;
+  const int slot = warp * spw + sub;
   const int nslots = NEWTON_WARPS * spw;
+  const unsigned submask = cpw == 32 ? 0xffffffffu : (((1u << cpw) - 1u) << (sub * cpw));
   const bool act = p < P && need[p];
   T acc[10];
 #pragma unroll
   for (int i = 0; i < 10; ++i) acc[i] = 0;
-  if (act) {
-    const T *e = evp + 8 * p;
-    T x = e[0], s = e[1];
-    const T *eap = ea + 2 * (long)p * W, *egp = eg + 2 * (long)p * W;
-    const T *pcp = pw + (2 * p) * NPW, *psp = pw + (2 * p + 1) * NPW;
-    const int npl = (L + 1) * (L + 1);
-    for (int q = slot; q < npl; q += nslots) {
+  T x = 0, s = 0;
+  const T *eap = ea + 2 * (long)p * W, *egp = eg + 2 * (long)p * W;
+  const T *pcp = pw + (2 * p) * NPW, *psp = pw + (2 * p + 1) * NPW;
+  if (act) { x = evp[8 * p]; s = evp[8 * p + 1]; }
+  // Each sub-slot walks order pairs q = slot, slot + nslots, ...; the next
+  // pair's entries are copied into the other half of the slot's shared
+  // buffer while the current pair is processed.
+  const int npl = (L + 1) * (L + 1);
+  const int BUFE = A.LJ + 1;
+  T *stg = (T *)sm.stage + (long)slot * 2 * (BUFE + 1) * 8;
+  auto issue = [&](int qq, int half) {
+    int mm = isqrt_floor(qq), len = L - mm + 1, off = pair_off[qq];
+    T *dst = stg + half * (BUFE + 1) * 8;
+    for (int e = p; e < len; e += cpw) {
+      copy_quad<T>(dst + 8 * e, cb + 4L * (off + e));
+      copy_quad<T>(dst + 8 * e + 4, rcoef + 4L * (off + e));
+    }
+    if (p == 0) copy_quad<T>(dst + 8 * BUFE, seedK + 4L * qq);  // (K, 0, 0, 0)
+  };
+  int cur = 0;
+  if (slot < npl) issue(slot, 0);
+  cp_async_commit();
+  for (int q = slot; q < npl; q += nslots) {
+    if (q + nslots < npl) issue(q + nslots, cur ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp(submask);
+    if (act) {
       int m = isqrt_floor(q), n = q - m * m - m;
-      int off = pair_off[q];
       T Acc[12];
-      pair_sum<T, FULL>(cb + 4L * off, rcoef + 4L * off, seedK[q], m, n, L, x, s, pcp, psp, Acc);
+      const T *st = stg + cur * (BUFE + 1) * 8;
+      pair_sum<T, FULL>(st, st[8 * BUFE], m, n, L, x, s, pcp, psp, Acc);
       // image (m, n) and its negation
       {
         T er = eap[2 * (m + L)] * egp[2 * (n + L)] - eap[2 * (m + L) + 1] * egp[2 * (n + L) + 1];
@@ -265,18 +313,19 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
         add_image<T, FULL>(acc, sg, n, m, zr0, zi0, zr1, zi1, zr2);
       }
     }
+    __syncwarp(submask);
+    cur ^= 1;
   }
+  cp_async_wait<0>();
   // reduce over the sub-slots of the warp that follow the same candidate
+  // (in the working precision; the cross-warp sum below is FP64)
   const int nq = FULL ? 10 : 1;
-  double accd[10];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) accd[i] = (double)acc[i];
   for (int o = cpw; o < 32; o <<= 1)
 #pragma unroll
     for (int i = 0; i < 10; ++i)
-      if (i < nq) accd[i] += __shfl_xor_sync(0xffffffffu, accd[i], o);
+      if (i < nq) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
   if (lane < cpw && p < P)
-    for (int i = 0; i < nq; ++i) sm.red[(warp * P + p) * 10 + i] = accd[i];
+    for (int i = 0; i < nq; ++i) sm.red[(warp * P + p) * 10 + i] = (double)acc[i];
   __syncthreads();
   for (int idx = tid; idx < P * nq; idx += blockDim.x) {
     int pp = idx / nq, i = idx - pp * nq;
@@ -376,6 +425,8 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   sm.ea = tp; tp += 2 * P * Wm;
   sm.eg = tp; tp += 2 * P * Wm;
   sm.pw = tp; tp += 2 * P * (2 * A.LJ + 3);
+  tp = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(tp) + 31) & ~uintptr_t(31));
+  sm.stage = tp;  // [slots][2][L_J+1][8]
 
   const int nc_b = n_cand[b];
   if (tid < P) {
@@ -480,7 +531,11 @@ size_t newton_smem_bytes(const Plan &p, size_t tsize) {
   size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
-  bytes += tsize * (8 * P + 4 * P * W + 2 * P * (2 * (size_t)p.LJ + 3));
+  bytes += tsize * (8 * P + 4 * P * W + 2 * P * (2 * (size_t)p.LJ + 3)) + 32;
+  int cpw = 1;
+  while (cpw < p.P) cpw <<= 1;
+  size_t slots = (size_t)NEWTON_WARPS * (32 / cpw);
+  bytes += tsize * slots * 2 * (p.LJ + 2) * 8;
   return bytes;
 }
 

@@ -115,10 +115,11 @@ __global__ void k_seedK(int npairs, double *K) {
   int m = 0;
   while ((m + 1) * (m + 1) <= q) ++m;
   int n = q - m * m - m;
-  // C(2m, m+n) = prod_{i=1}^{m-n} (m+n+i)/i
+  // C(2m, m+n) = prod_{i=1}^{m-n} (m+n+i)/i; stored as (K, 0, 0, 0)
   double c = 1.0;
   for (int i = 1; i <= m - n; ++i) c = c * (m + n + i) / i;
-  K[q] = sqrt(c);
+  K[4 * q] = sqrt(c);
+  K[4 * q + 1] = K[4 * q + 2] = K[4 * q + 3] = 0.0;
 }
 
 __device__ double ipow_d(double x, int p) {
@@ -137,7 +138,7 @@ __global__ void k_soft_d(int L0, int ns, int npairs0, const int *pair_off, const
   int n = q - m * m - m;
   double beta = M_PI * (2.0 * k + 1.0) / (2.0 * ns);
   double ch = cos(0.5 * beta), sh = sin(0.5 * beta), x = cos(beta);
-  double d = K[q] * ipow_d(ch, m + n) * ipow_d(-sh, m - n), dp = 0.0;
+  double d = K[4 * q] * ipow_d(ch, m + n) * ipow_d(-sh, m - n), dp = 0.0;
   double *o = out + (long)k * nc0 + pair_off0[q];
   const double *r = rc + 4L * pair_off[q];
   for (int l = m; l <= L0; ++l) {
@@ -156,7 +157,7 @@ __global__ void k_to_float(const double *in, float *out, long n) {
 cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
-  size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = p.npairs;
+  size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.npairs;
   double *gx, *gw;
   cudaError_t e;
   if ((e = cudaMalloc(&gx, sizeof(double) * 2 * p.S))) return e;

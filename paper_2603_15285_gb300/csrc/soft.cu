@@ -409,10 +409,221 @@ size_t soft_fused_smem(const Plan &p) {
 
 bool soft_fused_ok(const Plan &p) { return !p.fp64 && soft_fused_smem(p) <= 227 * 1024 - 1024; }
 
+// Streaming variant (both precisions): one CTA per particle walks the beta
+// slices k = 0..n-1, computing slice k+1 into a ring of three slices in
+// shared memory and then testing the local maxima of slice k, which needs
+// only slices k-1, k, k+1.  Under a strict total order no two neighbouring
+// grid points can both be local maxima, so one slice holds at most
+// ceil(n/2)^2 of them; they are merged by one warp into a running, sorted
+// list of the best P.  The grid itself never has to leave the chip; it is
+// written to grid_out only when that pointer is given.
+constexpr int STREAM_THREADS = 256;
+
+template <typename T>
+__device__ void stream_slice(const T *cb, int L0, int ns, int k,
+                             const int *__restrict__ pair_off, const T *__restrict__ soft_d,
+                             const int *__restrict__ pair_off0, long nc0, const T *__restrict__ tw,
+                             T *Sg, T *G, T *dst) {
+  const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1), tid = threadIdx.x, NT = blockDim.x;
+  const T *dk = soft_d + (long)k * nc0;
+  for (int q = tid; q < np0; q += NT) {
+    int m = isqrt_floor(q), n = q - m * m - m;
+    const T *cp = cb + 4L * pair_off0[q];  // staged copy, SOFFT layout
+    const T *dp = dk + pair_off0[q];
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    for (int l = m; l <= L0; ++l) {
+      T d = dp[l - m];
+      const T *e = cp + 4 * (l - m);
+      ar = fma(e[0], d, ar); ai = fma(e[1], d, ai);
+      br = fma(e[2], d, br); bi = fma(e[3], d, bi);
+    }
+    if ((m - n) & 1) { br = -br; bi = -bi; }  // d^l_nm = (-1)^{m-n} d^l_mn
+    int i0 = (m + L0) * W + (n + L0);
+    Sg[2 * i0] = ar; Sg[2 * i0 + 1] = ai;
+    if (q != 0) { int i1 = (-m + L0) * W + (-n + L0); Sg[2 * i1] = ar; Sg[2 * i1 + 1] = -ai; }
+    if (n != m && n != -m) {
+      int i2 = (n + L0) * W + (m + L0), i3 = (-n + L0) * W + (-m + L0);
+      Sg[2 * i2] = br; Sg[2 * i2 + 1] = bi;
+      Sg[2 * i3] = br; Sg[2 * i3 + 1] = -bi;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < (L0 + 1) * ns; t += NT) {  // G_m(j) = sum_n S_mn e^{i n g_j}
+    int m = t / ns, j = t - m * ns;
+    const T *row = Sg + 2 * (m + L0) * W;
+    T re = 0, im = 0;
+    int tt = (int)(((long)(-L0) * j) % ns);
+    if (tt < 0) tt += ns;
+    for (int n = -L0; n <= L0; ++n) {
+      T cr = tw[2 * tt], ci = tw[2 * tt + 1];
+      T sr = row[2 * (n + L0)], si = row[2 * (n + L0) + 1];
+      re += sr * cr - si * ci;
+      im += sr * ci + si * cr;
+      tt += j; if (tt >= ns) tt -= ns;
+    }
+    G[2 * t] = re; G[2 * t + 1] = im;
+  }
+  __syncthreads();
+  for (int t = tid; t < ns * ns; t += NT) {  // Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m a_i}
+    int i = t / ns, j = t - i * ns;
+    T acc = 0;
+    int tt = i;
+    for (int m = 1; m <= L0; ++m) {
+      T gr = G[2 * (m * ns + j)], gi = G[2 * (m * ns + j) + 1];
+      acc += gr * tw[2 * tt] - gi * tw[2 * tt + 1];
+      tt += i; if (tt >= ns) tt -= ns;
+    }
+    dst[t] = G[2 * j] + 2 * acc;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS)
+k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+              const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+              const T *__restrict__ tw, int P_max, const int *__restrict__ P_per,
+              T *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
+              double *__restrict__ score_out, int *__restrict__ n_cand_out) {
+  const long b = blockIdx.x;
+  const int W = 2 * L0 + 1, n2 = ns * ns, tid = threadIdx.x, NT = blockDim.x;
+  const int capc = ((ns + 1) / 2) * ((ns + 1) / 2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ring = reinterpret_cast<T *>(smem_raw);  // [3][n2]
+  T *Sg = ring + 3 * n2;                       // [W*W] complex
+  T *G = Sg + 2 * W * W;                       // [(L0+1)*ns] complex
+  T *cv = G + 2 * (L0 + 1) * ns;               // [capc] slice candidates
+  T *rv = cv + capc;                           // [32] running best values
+  int *ci = reinterpret_cast<int *>(rv + 32);  // [capc]
+  int *ri = ci + capc;                         // [32]
+  int *counters = ri + 32;                     // [0] slice count, [1] kept
+  T *cst = reinterpret_cast<T *>(reinterpret_cast<uintptr_t>(counters + 4) + 15 & ~uintptr_t(15));
+  // stage c^l_mn, l <= L0, of this particle in the SOFFT layout [nc0][4]
+  {
+    const T *cg = c + 4 * b * nc;
+    const int np0 = (L0 + 1) * (L0 + 1);
+    for (int t = threadIdx.x; t < np0 * (L0 + 1); t += blockDim.x) {
+      int q = t / (L0 + 1), e = t - q * (L0 + 1);
+      int m = isqrt_floor(q);
+      if (e <= L0 - m) {
+        const T *src = cg + 4L * (pair_off[q] + e);
+        T *dst = cst + 4L * (pair_off0[q] + e);
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+      }
+    }
+  }
+  const T *cb = cst;
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  if (tid < 32) { rv[tid] = 0; ri[tid] = INT_MAX; }
+  if (tid == 0) counters[1] = 0;
+  __syncthreads();
+  stream_slice(cb, L0, ns, 0, pair_off, soft_d, pair_off0, nc0, tw, Sg, G, ring);
+  if (ns > 1) stream_slice(cb, L0, ns, 1, pair_off, soft_d, pair_off0, nc0, tw, Sg, G, ring + n2);
+  for (int k = 0; k < ns; ++k) {
+    if (k >= 1 && k + 1 < ns)
+      stream_slice(cb, L0, ns, k + 1, pair_off, soft_d, pair_off0, nc0, tw, Sg, G,
+                   ring + ((k + 1) % 3) * n2);
+    const T *cur = ring + (k % 3) * n2;
+    if (grid_out) {
+      T *go = grid_out + b * (long)ns * n2;
+      for (int t = tid; t < n2; t += NT) {
+        int i = t / ns, j = t - i * ns;
+        go[((long)i * ns + k) * ns + j] = cur[t];
+      }
+    }
+    if (tid == 0) counters[0] = 0;
+    __syncthreads();
+    for (int t = tid; t < n2; t += NT) {
+      int i = t / ns, j = t - i * ns;
+      int p = (i * ns + k) * ns + j;
+      T v = cur[t];
+      bool ok = v == v;
+      for (int dk = -1; dk <= 1 && ok; ++dk) {
+        int kk = k + dk;
+        if (kk < 0 || kk >= ns) continue;
+        const T *sl = ring + (kk % 3) * n2;
+        for (int di = -1; di <= 1 && ok; ++di) {
+          int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+          for (int dj = -1; dj <= 1; ++dj) {
+            if (!di && !dk && !dj) continue;
+            int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+            int q = (ii * ns + kk) * ns + jj;
+            if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+          }
+        }
+      }
+      if (ok) {
+        int pos = atomicAdd(&counters[0], 1);
+        if (pos < capc) { cv[pos] = v; ci[pos] = p; }
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {  // warp 0: insert the slice's maxima into the sorted best-P list
+      const int lane = tid;
+      T myv = rv[lane];
+      int myi = ri[lane];
+      int kept = counters[1];
+      const int cnt = min(counters[0], capc);
+      for (int e = 0; e < cnt; ++e) {
+        T v = cv[e];
+        int i = ci[e];
+        bool before = lane < kept && precedes(myv, myi, v, i);
+        int pos = __popc(__ballot_sync(0xffffffffu, before));
+        T upv = __shfl_up_sync(0xffffffffu, myv, 1);
+        int upi = __shfl_up_sync(0xffffffffu, myi, 1);
+        if (pos < Pb) {
+          if (lane > pos) { myv = upv; myi = upi; }
+          if (lane == pos) { myv = v; myi = i; }
+          kept = min(kept + 1, Pb);
+        }
+      }
+      rv[lane] = myv;
+      ri[lane] = myi;
+      if (lane == 0) counters[1] = kept;
+    }
+    __syncthreads();
+  }
+  const int kept = counters[1];
+  for (int r = tid; r < P_max; r += NT) {
+    long o = b * P_max + r;
+    if (r < kept) {
+      int i = ri[r];
+      idx_out[o] = i;
+      score_out[o] = (double)rv[r];
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    } else {
+      idx_out[o] = -1;
+      score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+      euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+    }
+  }
+  if (tid == 0) n_cand_out[b] = kept;
+}
+
+size_t soft_stream_smem(const Plan &p, size_t ts) {
+  size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns, capc = (size_t)((p.ns + 1) / 2) * ((p.ns + 1) / 2);
+  return ts * (3 * n2 + 2 * W * W + 2 * (size_t)(p.L0 + 1) * p.ns + capc + 32) +
+         sizeof(int) * (capc + 32 + 4) + 32 + ts * 4 * (size_t)p.nc0;
+}
+
 template <typename T>
 cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
                         double *euler, double *score, int *n_cand, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  {
+    size_t smem = soft_stream_smem(p, sizeof(T));
+    if (smem <= 227 * 1024 - 1024) {
+      cudaFuncSetAttribute(k_soft_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_soft_stream<T><<<B, STREAM_THREADS, smem, st>>>(
+          c, p.nc, p.L0, p.ns, p.pair_off, (const T *)p.soft_d, p.pair_off0, p.nc0,
+          (const T *)p.soft_tw, p.P, P_per, grid, idx, euler, score, n_cand);
+      return cudaGetLastError();
+    }
+  }
   if (sizeof(T) == 4 && soft_fused_ok(p)) {
     size_t smem = soft_fused_smem(p);
     cudaFuncSetAttribute(k_soft_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
