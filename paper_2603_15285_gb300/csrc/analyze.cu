@@ -9,6 +9,7 @@
 // One CTA owns one (volume, shell): it gathers the n_theta * n_phi trilinear
 // samples into shared memory, folds the real DFT (pairs k, n_phi - k) and
 // runs the Legendre sums against the plan's table.
+#include <stdlib.h>
 #include "internal.cuh"
 
 namespace matcha {
@@ -105,9 +106,227 @@ k_analyze(const float *__restrict__ vols, int N, int S, int L, const double *__r
   }
 }
 
+// Shell-group kernel: one CTA per (volume, group of G shells).
+//  1. trilinear samples from per-ring constants (points near or outside the
+//     box edge take the bounds-checked path), folded on the fly into
+//     SP_k = f_k + f_{np-k}, SM_k = f_k - f_{np-k}, k = 1..np/2-1;
+//  2. the folded real DFT as two small matrix products
+//       Re F_m = f_0 + (-1)^m f_{np/2} + sum_k SP_k cos(2 pi m k/np)
+//       Im F_m = -sum_k SM_k sin(2 pi m k/np)
+//     register-tiled 4 rings x 4 orders per thread;
+//  3. the Legendre sums, one thread per (l, m) for all shells of the group.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  typedef float4 type;
+};
+template <> struct Vec4<double> {
+  struct type { double x, y, z, w; };
+};
+
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type ld4(const T *p) {
+  return *reinterpret_cast<const typename Vec4<T>::type *>(p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
+           const double *__restrict__ rs, const double *__restrict__ xj, const T *__restrict__ phi_cs,
+           const T *__restrict__ dcs, int Mp, const T *__restrict__ ptabT,
+           T *__restrict__ out) {
+  const int s0 = blockIdx.x * G;
+  const long b = blockIdx.y;
+  const int Gs = min(G, S - s0);
+  const int nt = L + 1, np = 2 * L + 2, half = np / 2, K1 = half - 1;
+  const int nlm = (L + 1) * (L + 2) / 2;
+  const int R = Gs * nt, Rp = (G * nt + 3) / 4 * 4;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *SP = reinterpret_cast<T *>(smem_raw);  // [K1][Rp]
+  T *SM = SP + K1 * Rp;                     // [K1][Rp]
+  T *E0 = SM + K1 * Rp;                     // [Rp]  f_0
+  T *EH = E0 + Rp;                          // [Rp]  f_{np/2}
+  T *CS = EH + Rp;                          // [2][K1][Mp]
+  T *F = CS + 2 * K1 * Mp;                  // [Rp][Mp] complex
+  T *RH = F + 2 * Rp * Mp;                  // [Rp] ring radius r_s sin(t_j)
+  T *RZ = RH + Rp;                          // [Rp] ring height c0 + r_s cos(t_j)
+  T *PH = RZ + Rp;                          // [np][2] cos, sin phi_k
+  const float *vol = vols + b * N * N * N;
+  const long NN = (long)N * N;
+
+  for (int t = tid; t < 2 * K1 * Mp; t += NT) CS[t] = dcs[t];
+  // zero the padding rings
+  for (int t = R + tid; t < Rp; t += NT) {
+    E0[t] = 0; EH[t] = 0;
+    for (int k = 0; k < K1; ++k) { SP[k * Rp + t] = 0; SM[k * Rp + t] = 0; }
+  }
+  // per-ring constants: rho = r_s sin(t_j), z = c0 + r_s cos(t_j)
+  for (int r = tid; r < R; r += NT) {
+    int sl = r / nt, j = r - sl * nt;
+    double rr = rs[s0 + sl], x = xj[j];
+    RH[r] = (T)(rr * sqrt(fmax(1.0 - x * x, 0.0)));
+    RZ[r] = (T)(0.5 * N + rr * x);
+  }
+  for (int t = tid; t < 2 * np; t += NT) PH[t] = phi_cs[t];
+  __syncthreads();
+  const T c0 = (T)(0.5 * N);
+  const T hi = (T)(N - 1);
+  // trilinear at (px, py, pz); corners clamped so that all eight are in the box
+  // when the point is (the value is unchanged), bounds-checked otherwise
+  auto sample = [&](T px, T py, T pz) -> T {
+    T fx = floor(px), fy = floor(py), fz = floor(pz);
+    bool inside = px >= T(0) && py >= T(0) && pz >= T(0) && px <= hi && py <= hi && pz <= hi;
+    if (inside) {
+      int i = min((int)fx, N - 2), j = min((int)fy, N - 2), k = min((int)fz, N - 2);
+      T tx = px - (T)i, ty = py - (T)j, tz = pz - (T)k;
+      const float *v = vol + ((long)k * N + j) * N + i;
+      T v000 = (T)__ldg(v), v001 = (T)__ldg(v + 1), v010 = (T)__ldg(v + N), v011 = (T)__ldg(v + N + 1);
+      T v100 = (T)__ldg(v + NN), v101 = (T)__ldg(v + NN + 1), v110 = (T)__ldg(v + NN + N),
+        v111 = (T)__ldg(v + NN + N + 1);
+      T a00 = v000 + tx * (v001 - v000), a01 = v010 + tx * (v011 - v010);
+      T a10 = v100 + tx * (v101 - v100), a11 = v110 + tx * (v111 - v110);
+      T b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
+      return b0 + tz * (b1 - b0);
+    }
+    int i3[3] = {(int)fx, (int)fy, (int)fz};
+    T f3[3] = {px - fx, py - fy, pz - fz};
+    T acc = 0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          int ii = i3[0] + dx, jj = i3[1] + dy, kk = i3[2] + dz;
+          if (ii < 0 || jj < 0 || kk < 0 || ii >= N || jj >= N || kk >= N) continue;
+          T wt = (dx ? f3[0] : T(1) - f3[0]) * (dy ? f3[1] : T(1) - f3[1]) * (dz ? f3[2] : T(1) - f3[2]);
+          acc += wt * (T)__ldg(vol + ((long)kk * N + jj) * N + ii);
+        }
+    return acc;
+  };
+  // 1. samples: item (ring r, kk), kk = 0..half-1, two samples each:
+  //    kk = 0 -> phi index 0 and np/2; kk >= 1 -> kk and np - kk
+  const int items = R * half;
+  for (int t0 = tid; t0 < items; t0 += 2 * NT) {
+    T va[2], vb[2];
+    int rr[2], kr[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int t = t0 + u * NT;
+      if (t >= items) t = t0;  // duplicate of the first item, not stored
+      int r = t / half, kk = t - r * half;
+      int ka = kk, kb = kk ? np - kk : half;
+      T rho = RH[r], pz = RZ[r];
+      va[u] = sample(c0 + rho * PH[2 * ka], c0 + rho * PH[2 * ka + 1], pz);
+      vb[u] = sample(c0 + rho * PH[2 * kb], c0 + rho * PH[2 * kb + 1], pz);
+      rr[u] = r; kr[u] = kk;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (t0 + u * NT >= items) continue;
+      int r = rr[u], kk = kr[u];
+      if (kk == 0) {
+        E0[r] = va[u]; EH[r] = vb[u];
+      } else {
+        SP[(kk - 1) * Rp + r] = va[u] + vb[u];
+        SM[(kk - 1) * Rp + r] = va[u] - vb[u];
+      }
+    }
+  }
+  __syncthreads();
+  // 2. folded DFT, 4 x 4 tiles of (ring, order)
+  const int tr = Rp / 4, tm = Mp / 4;
+  for (int t = tid; t < tr * tm; t += NT) {
+    int r0 = (t / tm) * 4, m0 = (t % tm) * 4;
+    T re[4][4], im[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { re[u][v] = 0; im[u][v] = 0; }
+    for (int k = 0; k < K1; ++k) {
+      typename Vec4<T>::type sp = ld4(SP + k * Rp + r0), sm = ld4(SM + k * Rp + r0);
+      typename Vec4<T>::type c = ld4(CS + k * Mp + m0), sn = ld4(CS + (K1 + k) * Mp + m0);
+      T spv[4] = {sp.x, sp.y, sp.z, sp.w}, smv[4] = {sm.x, sm.y, sm.z, sm.w};
+      T cv[4] = {c.x, c.y, c.z, c.w}, sv[4] = {sn.x, sn.y, sn.z, sn.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          re[u][v] = fma(spv[u], cv[v], re[u][v]);
+          im[u][v] = fma(-smv[u], sv[v], im[u][v]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      T e0 = E0[r0 + u], eh = EH[r0 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        int m = m0 + v;
+        T* o = F + 2 * ((r0 + u) * Mp + m);
+        o[0] = re[u][v] + e0 + ((m & 1) ? -eh : eh);
+        o[1] = im[u][v];
+      }
+    }
+  }
+  __syncthreads();
+  // 3. Legendre: f_lm(r_s) = sum_j ptab[j][lm] F_m(s, j)
+  for (int lm = tid; lm < nlm; lm += NT) {
+    int l = (int)((sqrtf(8.0f * lm + 1.0f) - 1.0f) * 0.5f);
+    while (l * (l + 1) / 2 > lm) --l;
+    while ((l + 1) * (l + 2) / 2 <= lm) ++l;
+    int m = lm - l * (l + 1) / 2;
+    T ar[8], ai[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) { ar[g] = 0; ai[g] = 0; }
+    for (int j = 0; j < nt; ++j) {
+      T w = ptabT[(long)j * nlm + lm];
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (g < Gs) {
+          const T *f = F + 2 * ((g * nt + j) * Mp + m);
+          ar[g] = fma(w, f[0], ar[g]);
+          ai[g] = fma(w, f[1], ai[g]);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      if (g < Gs) {
+        T *o = out + 2 * ((b * S + s0 + g) * (long)nlm + lm);
+        o[0] = ar[g];
+        o[1] = ai[g];
+      }
+  }
+}
+
+template <typename T>
+size_t analyze2_smem(const Plan &p, int G) {
+  int K1 = p.np / 2 - 1, Rp = (G * p.nt + 3) / 4 * 4;
+  return sizeof(T) * (2 * (size_t)K1 * Rp + 4 * (size_t)Rp + 2 * (size_t)K1 * p.Mp +
+                      2 * (size_t)Rp * p.Mp + 2 * (size_t)p.np);
+}
+
 template <typename T>
 cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  {
+    // shells per CTA: MATCHA_ANALYZE_SHELLS overrides the default (tuning)
+    static int G_env = -1;
+    if (G_env < 0) {
+      const char *e = getenv("MATCHA_ANALYZE_SHELLS");
+      G_env = e ? atoi(e) : 0;
+    }
+    int G = G_env > 0 ? min(G_env, 8) : (sizeof(T) == 8 ? 2 : 4);
+    while (G > 1 && analyze2_smem<T>(p, G) > 100 * 1024) --G;
+    size_t smem = analyze2_smem<T>(p, G);
+    if (smem <= 200 * 1024) {
+      static bool attr2[2] = {false, false};
+      if (!attr2[sizeof(T) == 8]) {
+        cudaFuncSetAttribute(k_analyze2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr2[sizeof(T) == 8] = true;
+      }
+      k_analyze2<T><<<dim3((p.S + G - 1) / G, B), 256, smem, st>>>(
+          vols, p.N, p.S, p.LJ, G, p.rs, p.xj, (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
+          (const T *)p.ptab, coef);
+      return cudaGetLastError();
+    }
+  }
   size_t smem = sizeof(T) * ((size_t)p.nt * p.np + 2 * (size_t)p.nt * (p.LJ + 1) + 2 * (size_t)p.np);
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(T) == 8]) {

@@ -26,6 +26,8 @@ struct Plan {
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
   void *rcoef;                  // real [nc][4]: (a, b, e, 0) of the step l -> l+1
   void *seedK;                  // real [npairs][4]: (sqrt(binom(2m, m+n)), 0, 0, 0)
+  void *dft_cs;                 // real [2][np/2-1][Mp]: cos, sin (2 pi m k / n_phi), k = 1..np/2-1
+  int Mp;                       // orders padded to a multiple of 4
   int *pair_off;                // [npairs] entry offset of pair q in the L_J layout
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 layout
   // host copies of the layout

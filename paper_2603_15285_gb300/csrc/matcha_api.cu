@@ -116,6 +116,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->npairs = (p->LJ + 1) * (p->LJ + 1);
   p->npairs0 = (p->L0 + 1) * (p->L0 + 1);
   p->ns = 2 * p->K * (p->L0 + 1);
+  p->Mp = (p->LJ + 1 + 3) / 4 * 4;
   p->nc = pair_entries_host(p->LJ);
   p->nc0 = pair_entries_host(p->L0);
   std::vector<int> off(p->npairs), off0(p->npairs0);
@@ -132,6 +133,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
   size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->npairs);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
+  size_t o_dcs = add(rs * 2 * (size_t)(p->np / 2 - 1) * p->Mp);
   cudaError_t e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
   char *b = (char *)p->base;
@@ -140,6 +142,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->ptab = b + o_pt; p->phi_cs = b + o_phi; p->soft_tw = b + o_tw; p->soft_d = b + o_sd;
   p->rcoef = b + o_rc; p->seedK = b + o_K;
   p->pair_off = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
+  p->dft_cs = b + o_dcs;
   p->h_pair_off = new int[p->npairs];
   memcpy(p->h_pair_off, off.data(), sizeof(int) * p->npairs);
   e = cudaMemcpy(p->pair_off, off.data(), 4 * p->npairs, cudaMemcpyHostToDevice);

@@ -394,6 +394,38 @@ __device__ int newton_dir(const double *g, const double *H, int L, double *d) {
   return fl;
 }
 
+// Candidate tid has C, grad, H of its current point in res: record C, stop on
+// a non-finite value (flag bit 0), take the Newton direction, stop the level
+// when the increment is below step_tol, else prepare the first trial.
+__device__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) {
+  const double *r = sm.res + 10 * tid;
+  double C = r[0], g[3] = {r[1], r[2], r[3]};
+  double H[9] = {r[4], r[5], r[6], r[5], r[7], r[8], r[6], r[8], r[9]};
+  bool fin = isfinite(C);
+  for (int i = 0; i < 3; ++i) fin = fin && isfinite(g[i]);
+  for (int i = 0; i < 9; ++i) fin = fin && isfinite(H[i]);
+  sm.Cc[tid] = C;
+  if (!fin) {
+    sm.fl[tid] |= 1;
+    sm.state[tid] = ST_DEAD;
+    return;
+  }
+  double d[3];
+  sm.fl[tid] |= newton_dir(g, H, L, d);
+  if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < A.tol) {
+    sm.state[tid] = ST_STOP;
+    return;
+  }
+  double tr[3] = {sm.th[3 * tid] + d[0], sm.th[3 * tid + 1] + d[1], sm.th[3 * tid + 2] + d[2]};
+  wrap_d(tr);
+  for (int i = 0; i < 3; ++i) {
+    sm.del[3 * tid + i] = d[i];
+    sm.tr[3 * tid + i] = tr[i];
+  }
+  sm.tries[tid] = 0;
+  sm.state[tid] = ST_TRIAL;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 2 : 3)
 k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__restrict__ rcoef,
@@ -440,75 +472,65 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   const T *cb = c + 4 * b * A.nc;
   long long work_full = 0, work_val = 0;  // counted by thread 0
 
+  // A trial point that is accepted is where the next step needs C, grad and
+  // H, so trials are evaluated with derivatives except on a level's last
+  // step: per level one derivative evaluation at the start point, then one
+  // evaluation per trial.  The points, the arithmetic at each point and the
+  // decisions are those of "evaluate at theta, step, test the trial".
   for (int lev = 0; lev < A.nlev; ++lev) {
     const int L = A.Ls[lev];
     // recurrence steps of one evaluation: sum_{m<=L} (2m+1)(L-m+1)
     long long steps_L = 0;
     for (int mm = 0; mm <= L; ++mm) steps_L += (long long)(2 * mm + 1) * (L - mm + 1);
-    if (tid < P && sm.state[tid] != ST_DEAD) sm.state[tid] = ST_RUN;
-    __syncthreads();
-    for (int t = 0; t < A.M; ++t) {
-      int want = 0;
-      if (tid < P) { need[tid] = sm.state[tid] == ST_RUN; want = need[tid]; }
-      if (!__syncthreads_or(want)) break;
-      if (tid == 0)
-        for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
-      evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
-      if (tid < P && need[tid]) {
-        const double *r = sm.res + 10 * tid;
-        double C = r[0], g[3] = {r[1], r[2], r[3]};
-        double H[9] = {r[4], r[5], r[6], r[5], r[7], r[8], r[6], r[8], r[9]};
-        bool fin = isfinite(C);
-        for (int i = 0; i < 3; ++i) fin = fin && isfinite(g[i]);
-        for (int i = 0; i < 9; ++i) fin = fin && isfinite(H[i]);
-        sm.Cc[tid] = C;
-        if (!fin) {
-          sm.fl[tid] |= 1;
-          sm.state[tid] = ST_DEAD;
-        } else {
-          double d[3];
-          sm.fl[tid] |= newton_dir(g, H, L, d);
-          if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < A.tol) {
-            sm.state[tid] = ST_STOP;
-          } else {
-            for (int i = 0; i < 3; ++i) { sm.del[3 * tid + i] = d[i]; }
-            double tr[3] = {sm.th[3 * tid] + d[0], sm.th[3 * tid + 1] + d[1], sm.th[3 * tid + 2] + d[2]};
-            wrap_d(tr);
-            for (int i = 0; i < 3; ++i) sm.tr[3 * tid + i] = tr[i];
-            sm.tries[tid] = 0;
-            sm.state[tid] = ST_TRIAL;
-          }
-        }
-      }
-      for (int h = 0; h < 3; ++h) {
-        int tw = 0;
-        if (tid < P) { need[tid] = sm.state[tid] == ST_TRIAL; tw = need[tid]; }
-        if (!__syncthreads_or(tw)) break;
-        if (tid == 0)
-          for (int q = 0; q < P; ++q) work_val += need[q] ? steps_L : 0;
-        evaluate<T, false>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
-        if (tid < P && need[tid]) {
-          double Ct = sm.res[10 * tid];
-          if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
-            for (int i = 0; i < 3; ++i) sm.th[3 * tid + i] = sm.tr[3 * tid + i];
-            sm.Cc[tid] = Ct;
-            sm.state[tid] = ST_RUN;
-          } else if (++sm.tries[tid] == 3) {
-            sm.fl[tid] |= 4;
-            sm.state[tid] = ST_STOP;
-          } else {
-            double tr[3];
-            for (int i = 0; i < 3; ++i) {
-              sm.del[3 * tid + i] *= 0.5;
-              tr[i] = sm.th[3 * tid + i] + sm.del[3 * tid + i];
-            }
-            wrap_d(tr);
-            for (int i = 0; i < 3; ++i) sm.tr[3 * tid + i] = tr[i];
-          }
-        }
-      }
-      __syncthreads();
+    int want = 0;
+    if (tid < P) { need[tid] = sm.state[tid] != ST_DEAD; want = need[tid]; }
+    if (!__syncthreads_or(want)) break;
+    if (tid == 0)
+      for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
+    evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
+    if (tid < P && need[tid]) {
+      sm.steps[tid] = 0;
+      start_step(tid, L, A, sm);
     }
+    for (int round = 0; round < 3 * A.M; ++round) {
+      int tw = 0, wf = 0;
+      if (tid < P) {
+        need[tid] = sm.state[tid] == ST_TRIAL;
+        tw = need[tid];
+        wf = tw && sm.steps[tid] < A.M - 1;
+      }
+      if (!__syncthreads_or(tw)) break;
+      const bool full = __syncthreads_or(wf);
+      if (tid == 0)
+        for (int q = 0; q < P; ++q) (full ? work_full : work_val) += need[q] ? steps_L : 0;
+      if (full) evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+      else evaluate<T, false>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+      if (tid < P && need[tid]) {
+        double Ct = sm.res[10 * tid];
+        if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
+          for (int i = 0; i < 3; ++i) sm.th[3 * tid + i] = sm.tr[3 * tid + i];
+          sm.Cc[tid] = Ct;
+          if (sm.steps[tid] < A.M - 1) {
+            ++sm.steps[tid];
+            start_step(tid, L, A, sm);  // derivatives at the accepted point
+          } else {
+            sm.state[tid] = ST_STOP;
+          }
+        } else if (++sm.tries[tid] == 3) {
+          sm.fl[tid] |= 4;
+          sm.state[tid] = ST_STOP;  // a repeated step from the same point rejects again
+        } else {
+          double tr[3];
+          for (int i = 0; i < 3; ++i) {
+            sm.del[3 * tid + i] *= 0.5;
+            tr[i] = sm.th[3 * tid + i] + sm.del[3 * tid + i];
+          }
+          wrap_d(tr);
+          for (int i = 0; i < 3; ++i) sm.tr[3 * tid + i] = tr[i];
+        }
+      }
+    }
+    __syncthreads();
   }
   if (tid < P) {
     long o = b * P + tid;

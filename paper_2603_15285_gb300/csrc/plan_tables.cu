@@ -149,6 +149,19 @@ __global__ void k_soft_d(int L0, int ns, int npairs0, const int *pair_off, const
   }
 }
 
+// Folded real DFT table: cs[0][k-1][m] = cos(2 pi m k / np), cs[1][k-1][m] =
+// sin(2 pi m k / np) for k = 1..np/2-1, m < Mp (zero for m > L).
+__global__ void k_dft_cs(int L, int Mp, double *cs) {
+  const int np = 2 * L + 2, K1 = np / 2 - 1;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K1 * Mp) return;
+  int k = t / Mp + 1, m = t % Mp;
+  double sv = 0.0, cv = 0.0;
+  if (m <= L) sincospi(2.0 * ((long)m * k % np) / np, &sv, &cv);
+  cs[t] = cv;
+  cs[K1 * Mp + t] = sv;
+}
+
 __global__ void k_to_float(const double *in, float *out, long n) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -158,6 +171,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
   size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.npairs;
+  size_t n_dcs = 2 * (size_t)(p.np / 2 - 1) * p.Mp;
   double *gx, *gw;
   cudaError_t e;
   if ((e = cudaMalloc(&gx, sizeof(double) * 2 * p.S))) return e;
@@ -166,7 +180,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   k_radial<<<(p.S + 63) / 64, 64, 0, st>>>(p.S, p.R, gx, gw, p.rs, p.wrad);
   k_gauss_legendre<<<(p.nt + 63) / 64, 64, 0, st>>>(p.nt, p.xj, p.wj);
   double *d64 = nullptr;
-  size_t tot = n_ptab + n_phi + n_tw + n_softd + n_rc + n_K;
+  size_t tot = n_ptab + n_phi + n_tw + n_softd + n_rc + n_K + n_dcs;
   if (!p.fp64) {
     if ((e = cudaMalloc(&d64, sizeof(double) * tot))) { cudaFree(gx); return e; }
   }
@@ -176,17 +190,20 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   double *sd = p.fp64 ? (double *)p.soft_d : tw + n_tw;
   double *rc = p.fp64 ? (double *)p.rcoef : sd + n_softd;
   double *K = p.fp64 ? (double *)p.seedK : rc + n_rc;
+  double *dcs = p.fp64 ? (double *)p.dft_cs : K + n_K;
   k_ptab<<<(unsigned)((n_ptab + 127) / 128), 128, 0, st>>>(p.LJ, p.nt, p.np, p.xj, p.wj, ptab);
   k_twiddle<<<(p.np + 127) / 128, 128, 0, st>>>(p.np, phi);
   k_twiddle<<<(p.ns + 127) / 128, 128, 0, st>>>(p.ns, tw);
   k_rcoef<<<p.npairs, 64, 0, st>>>(p.LJ, p.npairs, p.pair_off, rc);
   k_seedK<<<(p.npairs + 127) / 128, 128, 0, st>>>(p.npairs, K);
+  k_dft_cs<<<(unsigned)((n_dcs / 2 + 127) / 128), 128, 0, st>>>(p.LJ, p.Mp, dcs);
   k_soft_d<<<dim3(p.npairs0, p.ns), 32, 0, st>>>(p.L0, p.ns, p.npairs0, p.pair_off, p.pair_off0,
                                                  rc, K, p.nc0, sd);
   if (!p.fp64) {
     struct { double *src; void *dst; size_t n; } cp[] = {
         {ptab, p.ptab, n_ptab}, {phi, p.phi_cs, n_phi}, {tw, p.soft_tw, n_tw},
-        {sd, p.soft_d, n_softd}, {rc, p.rcoef, n_rc}, {K, p.seedK, n_K}};
+        {sd, p.soft_d, n_softd}, {rc, p.rcoef, n_rc}, {K, p.seedK, n_K},
+        {dcs, p.dft_cs, n_dcs}};
     for (auto &c : cp)
       k_to_float<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c.src, (float *)c.dst, (long)c.n);
   }
