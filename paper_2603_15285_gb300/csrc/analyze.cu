@@ -128,15 +128,15 @@ __device__ __forceinline__ typename Vec4<T>::type ld4(const T *p) {
   return *reinterpret_cast<const typename Vec4<T>::type *>(p);
 }
 
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(256)
-k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
+k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const double *__restrict__ rs, const double *__restrict__ xj, const T *__restrict__ phi_cs,
            const T *__restrict__ dcs, int Mp, const T *__restrict__ ptabT,
            T *__restrict__ out) {
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
-  const int Gs = min(G, S - s0);
+  const int Gs = G;  // the launcher picks G dividing S
   const int nt = L + 1, np = 2 * L + 2, half = np / 2, K1 = half - 1;
   const int nlm = (L + 1) * (L + 2) / 2;
   const int R = Gs * nt, Rp = (G * nt + 3) / 4 * 4;
@@ -161,8 +161,9 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
     for (int k = 0; k < K1; ++k) { SP[k * Rp + t] = 0; SM[k * Rp + t] = 0; }
   }
   // per-ring constants: rho = r_s sin(t_j), z = c0 + r_s cos(t_j)
+  const FastDiv dnt(nt), dhalf(half);
   for (int r = tid; r < R; r += NT) {
-    int sl = r / nt, j = r - sl * nt;
+    int sl = dnt.div(r), j = r - sl * nt;
     double rr = rs[s0 + sl], x = xj[j];
     RH[r] = (T)(rr * sqrt(fmax(1.0 - x * x, 0.0)));
     RZ[r] = (T)(0.5 * N + rr * x);
@@ -211,7 +212,7 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
     for (int u = 0; u < 2; ++u) {
       int t = t0 + u * NT;
       if (t >= items) t = t0;  // duplicate of the first item, not stored
-      int r = t / half, kk = t - r * half;
+      int r = dhalf.div(t), kk = t - r * half;
       int ka = kk, kb = kk ? np - kk : half;
       T rho = RH[r], pz = RZ[r];
       va[u] = sample(c0 + rho * PH[2 * ka], c0 + rho * PH[2 * ka + 1], pz);
@@ -233,8 +234,10 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
   __syncthreads();
   // 2. folded DFT, 4 x 4 tiles of (ring, order)
   const int tr = Rp / 4, tm = Mp / 4;
+  const FastDiv dtm(tm);
   for (int t = tid; t < tr * tm; t += NT) {
-    int r0 = (t / tm) * 4, m0 = (t % tm) * 4;
+    int tq = dtm.div(t);
+    int r0 = tq * 4, m0 = (t - tq * tm) * 4;
     T re[4][4], im[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -272,26 +275,25 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L, int G,
     while (l * (l + 1) / 2 > lm) --l;
     while ((l + 1) * (l + 2) / 2 <= lm) ++l;
     int m = lm - l * (l + 1) / 2;
-    T ar[8], ai[8];
+    T ar[G], ai[G];
 #pragma unroll
-    for (int g = 0; g < 8; ++g) { ar[g] = 0; ai[g] = 0; }
-    for (int j = 0; j < nt; ++j) {
+    for (int g = 0; g < G; ++g) { ar[g] = 0; ai[g] = 0; }
+    const T *fj = F + 2 * m;
+    for (int j = 0; j < nt; ++j, fj += 2 * Mp) {
       T w = ptabT[(long)j * nlm + lm];
 #pragma unroll
-      for (int g = 0; g < 8; ++g)
-        if (g < Gs) {
-          const T *f = F + 2 * ((g * nt + j) * Mp + m);
-          ar[g] = fma(w, f[0], ar[g]);
-          ai[g] = fma(w, f[1], ai[g]);
-        }
+      for (int g = 0; g < G; ++g) {
+        const T *f = fj + 2 * g * nt * Mp;
+        ar[g] = fma(w, f[0], ar[g]);
+        ai[g] = fma(w, f[1], ai[g]);
+      }
     }
 #pragma unroll
-    for (int g = 0; g < 8; ++g)
-      if (g < Gs) {
-        T *o = out + 2 * ((b * S + s0 + g) * (long)nlm + lm);
-        o[0] = ar[g];
-        o[1] = ai[g];
-      }
+    for (int g = 0; g < G; ++g) {
+      T *o = out + 2 * ((b * S + s0 + g) * (long)nlm + lm);
+      o[0] = ar[g];
+      o[1] = ai[g];
+    }
   }
 }
 
@@ -306,24 +308,24 @@ template <typename T>
 cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   {
-    // shells per CTA: MATCHA_ANALYZE_SHELLS overrides the default (tuning)
+    // shells per CTA: a divisor of S in {8, 4, 2, 1} whose shared memory fits
+    // (MATCHA_ANALYZE_SHELLS overrides the preferred size, for tuning)
     static int G_env = -1;
     if (G_env < 0) {
       const char *e = getenv("MATCHA_ANALYZE_SHELLS");
       G_env = e ? atoi(e) : 0;
     }
-    int G = G_env > 0 ? min(G_env, 8) : (sizeof(T) == 8 ? 2 : 4);
-    while (G > 1 && analyze2_smem<T>(p, G) > 100 * 1024) --G;
+    int G = G_env > 0 ? G_env : 2;
+    G = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
+    while (G > 1 && (p.S % G != 0 || analyze2_smem<T>(p, G) > 100 * 1024)) G >>= 1;
     size_t smem = analyze2_smem<T>(p, G);
     if (smem <= 200 * 1024) {
-      static bool attr2[2] = {false, false};
-      if (!attr2[sizeof(T) == 8]) {
-        cudaFuncSetAttribute(k_analyze2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr2[sizeof(T) == 8] = true;
-      }
-      k_analyze2<T><<<dim3((p.S + G - 1) / G, B), 256, smem, st>>>(
-          vols, p.N, p.S, p.LJ, G, p.rs, p.xj, (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
-          (const T *)p.ptab, coef);
+      auto kern = G == 8 ? k_analyze2<T, 8> : G == 4 ? k_analyze2<T, 4> : G == 2 ? k_analyze2<T, 2>
+                                                                                  : k_analyze2<T, 1>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<dim3(p.S / G, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj,
+                                                (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
+                                                (const T *)p.ptab, coef);
       return cudaGetLastError();
     }
   }

@@ -69,6 +69,20 @@ cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const in
 // Small device helpers.
 template <typename T> struct Cplx { T x, y; };
 
+// Exact division of small non-negative ints by a runtime divisor without the
+// emulated integer divide: a float reciprocal estimate, then one correction.
+struct FastDiv {
+  int d;
+  float inv;
+  __device__ __forceinline__ explicit FastDiv(int dd) : d(dd), inv(1.0f / (float)dd) {}
+  __device__ __forceinline__ int div(int x) const {
+    int q = __float2int_rz(((float)x + 0.5f) * inv);
+    if (q * d > x) --q;
+    else if ((q + 1) * d <= x) ++q;
+    return q;
+  }
+};
+
 __device__ __forceinline__ int isqrt_floor(int q) {
   int m = (int)sqrtf((float)q);
   while (m * m > q) --m;

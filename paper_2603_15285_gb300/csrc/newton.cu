@@ -221,9 +221,10 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
     e[6] = tcos(ga); e[7] = tsin(ga);
   }
   __syncthreads();
+  const FastDiv dw(2 * L + 3);
   for (int t = tid; t < 2 * P * (2 * L + 3); t += blockDim.x) {
-    int p = t / (2 * (2 * L + 3)), r = t - p * 2 * (2 * L + 3);
-    int which = r / (2 * L + 3), k = r - which * (2 * L + 3);
+    int pr = dw.div(t), k = t - pr * (2 * L + 3);
+    int p = pr >> 1, which = pr & 1;
     if (need[p]) pw[(2 * p + which) * NPW + k] = ipow_t(evp[8 * p + 2 + which], k);
   }
   if (tid < 2 * P) {

@@ -448,12 +448,13 @@ __device__ void stream_slice(const T *cb, int L0, int ns, int k,
     }
   }
   __syncthreads();
+  const FastDiv dns(ns);
   for (int t = tid; t < (L0 + 1) * ns; t += NT) {  // G_m(j) = sum_n S_mn e^{i n g_j}
-    int m = t / ns, j = t - m * ns;
+    int m = dns.div(t), j = t - m * ns;
     const T *row = Sg + 2 * (m + L0) * W;
     T re = 0, im = 0;
-    int tt = (int)(((long)(-L0) * j) % ns);
-    if (tt < 0) tt += ns;
+    int tt = ns - (L0 * j - dns.div(L0 * j) * ns);  // (-L0 j) mod ns
+    if (tt >= ns) tt -= ns;
     for (int n = -L0; n <= L0; ++n) {
       T cr = tw[2 * tt], ci = tw[2 * tt + 1];
       T sr = row[2 * (n + L0)], si = row[2 * (n + L0) + 1];
@@ -465,7 +466,7 @@ __device__ void stream_slice(const T *cb, int L0, int ns, int k,
   }
   __syncthreads();
   for (int t = tid; t < ns * ns; t += NT) {  // Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m a_i}
-    int i = t / ns, j = t - i * ns;
+    int i = dns.div(t), j = t - i * ns;
     T acc = 0;
     int tt = i;
     for (int m = 1; m <= L0; ++m) {
@@ -502,8 +503,9 @@ k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__res
   {
     const T *cg = c + 4 * b * nc;
     const int np0 = (L0 + 1) * (L0 + 1);
+    const FastDiv dl(L0 + 1);
     for (int t = threadIdx.x; t < np0 * (L0 + 1); t += blockDim.x) {
-      int q = t / (L0 + 1), e = t - q * (L0 + 1);
+      int q = dl.div(t), e = t - q * (L0 + 1);
       int m = isqrt_floor(q);
       if (e <= L0 - m) {
         const T *src = cg + 4L * (pair_off[q] + e);
@@ -525,24 +527,26 @@ k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__res
       stream_slice(cb, L0, ns, k + 1, pair_off, soft_d, pair_off0, nc0, tw, Sg, G,
                    ring + ((k + 1) % 3) * n2);
     const T *cur = ring + (k % 3) * n2;
+    const T *sls[3] = {ring + ((k + 2) % 3) * n2, cur, ring + ((k + 1) % 3) * n2};
+    const FastDiv dns(ns);
     if (grid_out) {
       T *go = grid_out + b * (long)ns * n2;
       for (int t = tid; t < n2; t += NT) {
-        int i = t / ns, j = t - i * ns;
+        int i = dns.div(t), j = t - i * ns;
         go[((long)i * ns + k) * ns + j] = cur[t];
       }
     }
     if (tid == 0) counters[0] = 0;
     __syncthreads();
     for (int t = tid; t < n2; t += NT) {
-      int i = t / ns, j = t - i * ns;
+      int i = dns.div(t), j = t - i * ns;
       int p = (i * ns + k) * ns + j;
       T v = cur[t];
       bool ok = v == v;
       for (int dk = -1; dk <= 1 && ok; ++dk) {
         int kk = k + dk;
         if (kk < 0 || kk >= ns) continue;
-        const T *sl = ring + (kk % 3) * n2;
+        const T *sl = sls[dk + 1];
         for (int di = -1; di <= 1 && ok; ++di) {
           int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
           for (int dj = -1; dj <= 1; ++dj) {
