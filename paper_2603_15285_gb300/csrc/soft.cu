@@ -608,6 +608,260 @@ k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__res
   if (tid == 0) n_cand_out[b] = kept;
 }
 
+// Chunked streaming variant: each pass computes up to KB+1 new beta slices at
+// once (three phases over all of them) into a ring of KB+2 slices, then tests
+// the local maxima of KB slices and merges them, so each barrier separates
+// KB times more independent work than the one-slice version.
+constexpr int CHUNK_THREADS = 512;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { struct type { double x, y, z, w; }; };
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type ld4(const T *p) {
+  return *reinterpret_cast<const typename Vec4<T>::type *>(p);
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(CHUNK_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+             const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+             const T *__restrict__ tw, int P_max, const int *__restrict__ P_per,
+             T *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
+             double *__restrict__ score_out, int *__restrict__ n_cand_out) {
+  constexpr int NR = KB + 2;
+  const long b = blockIdx.x;
+  const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1), n2 = ns * ns;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int capc = KB * ((ns + 1) / 2) * ((ns + 1) / 2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // every section starts on a multiple of 4 elements (16-byte vector loads)
+  auto al4 = [](long x) { return (x + 3) & ~3L; };
+  T *ring = reinterpret_cast<T *>(smem_raw);   // [NR][n2]
+  T *Sg = ring + al4(NR * n2);                  // [KB+1][W*W] complex
+  const int nsp = (ns + 3) / 4 * 4, nq4 = nsp / 4;
+  T *G = Sg + al4((KB + 1) * 2 * W * W);        // [KB+1][L0+1][re|im][nsp]
+  T *Eg = G + al4((KB + 1) * 2 * (L0 + 1) * nsp);  // [W][nsp] complex: e^{i n g_j}
+  T *Aa = Eg + al4(2 * W * nsp);                // [2(L0+1)][nsp]: w_m (cos m a_i, -sin m a_i)
+  T *cst = Aa + al4(2 * (L0 + 1) * nsp);        // [nc0][4] staged c, l <= L0
+  T *cv = cst + 4 * nc0;                        // [capc]
+  T *rv = cv + capc;                            // [32]
+  int *ci = reinterpret_cast<int *>(rv + 32);   // [capc]
+  int *ri = ci + capc;                          // [32]
+  int *counters = ri + 32;                      // [0] pass count, [1] kept
+  const FastDiv dns(ns), dn2(n2), dnp0(np0), dl(L0 + 1);
+  const FastDiv dq4(nq4), dmq((L0 + 1) * nq4), dqq(nq4 * nq4);
+  // twiddle tables (angles 2 pi t / ns from the plan's table)
+  for (int t = tid; t < W * nsp; t += NT) {
+    int n = t / nsp, j = t - n * nsp;
+    T er = 0, ei = 0;
+    if (j < ns) {
+      int tt = ((n - L0) * j) % ns;
+      if (tt < 0) tt += ns;
+      er = tw[2 * tt]; ei = tw[2 * tt + 1];
+    }
+    Eg[2 * t] = er; Eg[2 * t + 1] = ei;
+  }
+  for (int t = tid; t < 2 * (L0 + 1) * nsp; t += NT) {
+    int cc = t / nsp, i = t - cc * nsp, m = cc >> 1;
+    T v = 0;
+    if (i < ns) {
+      int tt = (m * i) % ns;
+      T w = m == 0 ? T(1) : T(2);
+      v = (cc & 1) ? -w * tw[2 * tt + 1] : w * tw[2 * tt];
+    }
+    Aa[t] = v;
+  }
+  {
+    const T *cg = c + 4 * b * nc;
+    for (int t = tid; t < np0 * (L0 + 1); t += NT) {
+      int q = dl.div(t), e = t - q * (L0 + 1);
+      int m = isqrt_floor(q);
+      if (e <= L0 - m) {
+        const T *src = cg + 4L * (pair_off[q] + e);
+        T *dst = cst + 4L * (pair_off0[q] + e);
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+      }
+    }
+  }
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  if (tid < 32) { rv[tid] = 0; ri[tid] = INT_MAX; }
+  if (tid == 0) counters[1] = 0;
+  __syncthreads();
+  int done = 0;  // slices [0, done) computed
+  for (int k0 = 0; k0 < ns; k0 += KB) {
+    const int hi = min(ns, k0 + KB + 1), ka = done, nk = hi - ka;
+    // phase 1: beta transform of slices ka..hi-1
+    for (int t = tid; t < nk * np0; t += NT) {
+      int kk = dnp0.div(t), q = t - kk * np0, k = ka + kk;
+      int m = isqrt_floor(q), n = q - m * m - m;
+      const T *cp = cst + 4L * pair_off0[q];
+      const T *dp = soft_d + (long)k * nc0 + pair_off0[q];
+      T ar = 0, ai = 0, br = 0, bi = 0;
+      for (int l = m; l <= L0; ++l) {
+        T d = dp[l - m];
+        const T *e = cp + 4 * (l - m);
+        ar = fma(e[0], d, ar); ai = fma(e[1], d, ai);
+        br = fma(e[2], d, br); bi = fma(e[3], d, bi);
+      }
+      if ((m - n) & 1) { br = -br; bi = -bi; }  // d^l_nm = (-1)^{m-n} d^l_mn
+      T *S = Sg + kk * 2 * W * W;
+      int i0 = (m + L0) * W + (n + L0);
+      S[2 * i0] = ar; S[2 * i0 + 1] = ai;
+      if (q != 0) { int i1 = (-m + L0) * W + (-n + L0); S[2 * i1] = ar; S[2 * i1 + 1] = -ai; }
+      if (n != m && n != -m) {
+        int i2 = (n + L0) * W + (m + L0), i3 = (-n + L0) * W + (-m + L0);
+        S[2 * i2] = br; S[2 * i2 + 1] = bi;
+        S[2 * i3] = br; S[2 * i3 + 1] = -bi;
+      }
+    }
+    __syncthreads();
+    // phase 2: G_m(j) = sum_n S_mn e^{i n g_j}; tiles of one m and 4 j
+    for (int t = tid; t < nk * (L0 + 1) * nq4; t += NT) {
+      int kk = dmq.div(t), r = t - kk * (L0 + 1) * nq4;
+      int m = dq4.div(r), j0 = (r - m * nq4) * 4;
+      const T *row = Sg + kk * 2 * W * W + 2 * (m + L0) * W;
+      T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+      for (int n = 0; n < W; ++n) {
+        T sr = row[2 * n], si = row[2 * n + 1];
+        const T *e = Eg + 2 * (n * nsp + j0);
+        typename Vec4<T>::type e01 = ld4(e), e23 = ld4(e + 4);
+        T er[4] = {e01.x, e01.z, e23.x, e23.z}, ei[4] = {e01.y, e01.w, e23.y, e23.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          re[u] = fma(sr, er[u], fma(-si, ei[u], re[u]));
+          im[u] = fma(sr, ei[u], fma(si, er[u], im[u]));
+        }
+      }
+      T *Gk = G + kk * 2 * (L0 + 1) * nsp + 2 * m * nsp;  // [m][re|im][j]
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { Gk[j0 + u] = re[u]; Gk[nsp + j0 + u] = im[u]; }
+    }
+    __syncthreads();
+    // phase 3: C(i, k, j) = sum_c A[c][i] B[c][j] with c = (m, re/im),
+    // A = w_m (cos m a_i, -sin m a_i), B = (Re G_m(j), Im G_m(j)); 4 x 4 tiles
+    for (int t = tid; t < nk * nq4 * nq4; t += NT) {
+      int kk = dqq.div(t), r = t - kk * nq4 * nq4;
+      int iq = dq4.div(r), i0 = iq * 4, j0 = (r - iq * nq4) * 4;
+      const T *Bk = G + kk * 2 * (L0 + 1) * nsp;
+      T o[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) o[u][v] = 0;
+      for (int cc = 0; cc < 2 * (L0 + 1); ++cc) {
+        typename Vec4<T>::type av = ld4(Aa + cc * nsp + i0), bv = ld4(Bk + cc * nsp + j0);
+        T a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) o[u][v] = fma(a4[u], b4[v], o[u][v]);
+      }
+      T *dst = ring + ((ka + kk) % NR) * n2;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (i0 + u < ns && j0 + v < ns) dst[(i0 + u) * ns + j0 + v] = o[u][v];
+    }
+    done = hi;
+    if (tid == 0) counters[0] = 0;
+    __syncthreads();
+    const int k1 = min(ns, k0 + KB), nt_ = k1 - k0;
+    if (grid_out) {
+      T *go = grid_out + b * (long)ns * n2;
+      for (int t = tid; t < nt_ * n2; t += NT) {
+        int kk = dn2.div(t), r = t - kk * n2;
+        int i = dns.div(r), j = r - i * ns, k = k0 + kk;
+        go[((long)i * ns + k) * ns + j] = ring[(k % NR) * n2 + r];
+      }
+    }
+    // local maxima of slices k0..k1-1
+    for (int t = tid; t < nt_ * n2; t += NT) {
+      int kk = dn2.div(t), r = t - kk * n2, k = k0 + kk;
+      int i = dns.div(r), j = r - i * ns;
+      int p = (i * ns + k) * ns + j;
+      T v = ring[(k % NR) * n2 + r];
+      bool ok = v == v;
+      for (int dk = -1; dk <= 1 && ok; ++dk) {
+        int kq = k + dk;
+        if (kq < 0 || kq >= ns) continue;
+        const T *sl = ring + (kq % NR) * n2;
+        for (int di = -1; di <= 1 && ok; ++di) {
+          int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+          for (int dj = -1; dj <= 1; ++dj) {
+            if (!di && !dk && !dj) continue;
+            int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+            int q = (ii * ns + kq) * ns + jj;
+            if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+          }
+        }
+      }
+      if (ok) {
+        int pos = atomicAdd(&counters[0], 1);
+        if (pos < capc) { cv[pos] = v; ci[pos] = p; }
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {  // warp 0: insert into the sorted best-P list
+      const int lane = tid;
+      T myv = rv[lane];
+      int myi = ri[lane];
+      int kept = counters[1];
+      const int cnt = min(counters[0], capc);
+      for (int e = 0; e < cnt; ++e) {
+        T v = cv[e];
+        int i = ci[e];
+        bool before = lane < kept && precedes(myv, myi, v, i);
+        int pos = __popc(__ballot_sync(0xffffffffu, before));
+        T upv = __shfl_up_sync(0xffffffffu, myv, 1);
+        int upi = __shfl_up_sync(0xffffffffu, myi, 1);
+        if (pos < Pb) {
+          if (lane > pos) { myv = upv; myi = upi; }
+          if (lane == pos) { myv = v; myi = i; }
+          kept = min(kept + 1, Pb);
+        }
+      }
+      rv[lane] = myv;
+      ri[lane] = myi;
+      if (lane == 0) counters[1] = kept;
+    }
+    __syncthreads();
+  }
+  const int kept = counters[1];
+  for (int r = tid; r < P_max; r += NT) {
+    long o = b * P_max + r;
+    if (r < kept) {
+      int i = ri[r];
+      idx_out[o] = i;
+      score_out[o] = (double)rv[r];
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    } else {
+      idx_out[o] = -1;
+      score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+      euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+    }
+  }
+  if (tid == 0) n_cand_out[b] = kept;
+}
+
+constexpr int SOFT_KB = 4;
+
+size_t soft_chunk_smem(const Plan &p, size_t ts) {
+  size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns;
+  size_t capc = (size_t)SOFT_KB * ((p.ns + 1) / 2) * ((p.ns + 1) / 2);
+  size_t nsp = (size_t)(p.ns + 3) / 4 * 4;
+  auto al4 = [](size_t x) { return (x + 3) & ~size_t(3); };
+  return ts * (al4((SOFT_KB + 2) * n2) + al4((SOFT_KB + 1) * 2 * W * W) +
+               al4((SOFT_KB + 1) * 2 * (size_t)(p.L0 + 1) * nsp) + al4(2 * W * nsp) +
+               al4(2 * (size_t)(p.L0 + 1) * nsp) + 4 * (size_t)p.nc0 + capc + 32) +
+         sizeof(int) * (capc + 32 + 4) + 16;
+}
+
 size_t soft_stream_smem(const Plan &p, size_t ts) {
   size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns, capc = (size_t)((p.ns + 1) / 2) * ((p.ns + 1) / 2);
   return ts * (3 * n2 + 2 * W * W + 2 * (size_t)(p.L0 + 1) * p.ns + capc + 32) +
@@ -618,6 +872,17 @@ template <typename T>
 cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
                         double *euler, double *score, int *n_cand, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  {
+    size_t smem = soft_chunk_smem(p, sizeof(T));
+    if (smem <= 227 * 1024 - 1024) {
+      cudaFuncSetAttribute(k_soft_chunk<T, SOFT_KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      k_soft_chunk<T, SOFT_KB><<<B, CHUNK_THREADS, smem, st>>>(
+          c, p.nc, p.L0, p.ns, p.pair_off, (const T *)p.soft_d, p.pair_off0, p.nc0,
+          (const T *)p.soft_tw, p.P, P_per, grid, idx, euler, score, n_cand);
+      return cudaGetLastError();
+    }
+  }
   {
     size_t smem = soft_stream_smem(p, sizeof(T));
     if (smem <= 227 * 1024 - 1024) {
