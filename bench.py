@@ -127,6 +127,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def newton_traffic(B):
+    """DRAM bytes per Newton launch from the committed ncu capture, scaled to
+    B particles; None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        meta = json.load(open(os.path.join(ROOT, "profiles", "k_newton_traffic.json")))
+        src = open(os.path.join(ROOT, meta["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != meta.get("sha256"):
+        return None
+    return meta["dram_bytes_per_launch_1024"] * B / 1024.0
+
+
 def run_reference(args):
     """The oracle (FP64 C, all host cores) on a bounded sample of the workload."""
     ws, rank, _ = dist_env()
@@ -273,7 +287,8 @@ def main():
         "config": workload_config(w, B, ws),
         "stage_ms": stage_ms,
         "roofline": {"kernel": "k_newton", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": newton_traffic(B) if prec == m.FP32 else None,
                      "peak_source": "%d SMs x %d %s lanes x 2 x %.0f MHz (max SM clock seen)"
                                     % (SMS, FP32_LANES if prec == m.FP32 else 2,
                                        "FP32" if prec == m.FP32 else "FP64", clk),
