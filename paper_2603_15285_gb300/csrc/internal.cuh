@@ -32,6 +32,9 @@ struct Plan {
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 layout
   // host copies of the layout
   int *h_pair_off = nullptr;
+  // copy stream and events of matcha_align_host (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev[9] = {};
 };
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }

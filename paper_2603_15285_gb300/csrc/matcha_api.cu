@@ -162,6 +162,9 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
   if (!plan) return MATCHA_OK;
   Plan *p = P_(plan);
   cudaDeviceSynchronize();
+  for (auto &ev : p->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   cudaError_t e = cudaFree(p->base);
   delete[] p->h_pair_off;
   delete p;
@@ -308,13 +311,21 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
                              best_p, flags, stream);
 }
 
+// Host-buffer path: the batch is split into up to 4 chunks; chunk i+1 is copied
+// to the device on the plan's copy stream while chunk i is aligned on the
+// caller's stream (host-to-device bandwidth, not compute, bounds this path).
+static int host_chunk(int B) {
+  int ch = (B + 3) / 4;
+  return ch < 256 ? (B < 256 ? B : 256) : ch;
+}
+
 matcha_status matcha_host_workspace_size(matcha_plan plan, int B, int tstride, size_t *bytes) {
   if (!plan || !bytes || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
   Plan *p = P_(plan);
   AlignWs w;
-  const int Bt = tstride ? B : 1;
+  const int Bt = tstride ? B : 1, CH = host_chunk(B);
   size_t vox = (size_t)p->N * p->N * p->N;
-  size_t sz = align_up(carve_align(*p, B, Bt, nullptr, &w));
+  size_t sz = align_up(carve_align(*p, CH, tstride ? CH : 1, nullptr, &w));
   sz += align_up(sizeof(float) * vox * B) + align_up(sizeof(float) * vox * Bt);
   sz += align_up(sizeof(double) * 13 * B) + align_up(sizeof(int) * 2 * B);
   *bytes = sz;
@@ -334,21 +345,43 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
   if (s) return s;
   if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
   Plan *p = P_(plan);
-  const int Bt = tstride ? B : 1;
+  if (!p->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    for (auto &ev : p->ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  const int Bt = tstride ? B : 1, CH = host_chunk(B);
   AlignWs w;
-  size_t inner = align_up(carve_align(*p, B, Bt, nullptr, &w));
+  size_t inner = align_up(carve_align(*p, CH, tstride ? CH : 1, nullptr, &w));
   Carve cv{(char *)ws + inner};
   size_t vox = (size_t)p->N * p->N * p->N;
   float *dpart = cv.take<float>(vox * B);
   float *dtemp = cv.take<float>(vox * Bt);
   double *dout = cv.take<double>(13 * (size_t)B);
   int *iout = cv.take<int>(2 * (size_t)B);
-  cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(dpart, particles, sizeof(float) * vox * B, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dtemp, templates, sizeof(float) * vox * Bt, cudaMemcpyHostToDevice, st));
-  s = matcha_align(plan, dpart, dtemp, B, tstride, nullptr, dout, dout + 3 * B, dout + 12 * B, iout,
-                   iout + B, ws, inner, stream);
-  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream, cs = p->copy_stream;
+  const int nch = (B + CH - 1) / CH;
+  // the copies must not overtake earlier work of the caller's stream
+  CK(cudaEventRecord(p->ev[8], st));
+  CK(cudaStreamWaitEvent(cs, p->ev[8], 0));
+  if (!tstride) CK(cudaMemcpyAsync(dtemp, templates, sizeof(float) * vox, cudaMemcpyHostToDevice, cs));
+  for (int c = 0; c < nch; ++c) {
+    size_t b0 = (size_t)c * CH, nb = (size_t)(B - (int)b0 < CH ? B - (int)b0 : CH);
+    CK(cudaMemcpyAsync(dpart + b0 * vox, particles + b0 * vox, sizeof(float) * vox * nb,
+                       cudaMemcpyHostToDevice, cs));
+    if (tstride)
+      CK(cudaMemcpyAsync(dtemp + b0 * vox, templates + b0 * vox, sizeof(float) * vox * nb,
+                         cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(p->ev[c], cs));
+  }
+  for (int c = 0; c < nch; ++c) {
+    size_t b0 = (size_t)c * CH;
+    int nb = B - (int)b0 < CH ? B - (int)b0 : CH;
+    CK(cudaStreamWaitEvent(st, p->ev[c], 0));
+    s = matcha_align(plan, dpart + b0 * vox, tstride ? dtemp + b0 * vox : dtemp, nb, tstride,
+                     nullptr, dout + 3 * b0, dout + 3 * B + 9 * b0, dout + 12 * B + b0, iout + b0,
+                     iout + B + b0, ws, inner, stream);
+    if (s) return s;
+  }
   CK(cudaMemcpyAsync(euler, dout, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(R, dout + 3 * B, sizeof(double) * 9 * B, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(score, dout + 12 * B, sizeof(double) * B, cudaMemcpyDeviceToHost, st));

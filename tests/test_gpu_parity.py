@@ -238,3 +238,16 @@ def test_soft_grid_and_top_p_fp32(w):
         assert np.abs(ggot - gref).max() <= 1e-5 * np.abs(gref).max()
         nc = int(s["n_cand"][b])
         assert list(s["idx"][b, :nc].cpu().numpy()) == _brute_top_p(ggot, n, w.P)
+
+
+def test_host_buffers_in_several_chunks_match_device_path():
+    """600 particles: the host path copies and aligns them in 3 chunks."""
+    w = dataclasses.replace(SMALL, B=600)
+    d, parts, temps = gen(w)
+    plan = m.plan_for_workload(w, precision=m.FP32)
+    dev = m.matcha_align(plan, parts, temps)
+    hp = d["particles"].pin_memory()
+    ht = d["templates"].pin_memory()
+    host = m.matcha_align_host(plan, hp, ht)
+    assert np.array_equal(host["R"], dev["R"].cpu().numpy())
+    assert np.array_equal(host["best_p"], dev["best_p"].cpu().numpy())
