@@ -107,77 +107,128 @@ template <> struct Quad<double> {
   __device__ __forceinline__ double w() const { return b.y; }
 };
 
-// Accumulates the contributions of one order pair for one candidate.
+// Accumulates the contributions of one order pair for NC candidates that
+// share the pair's staged entries (one lane carries NC candidates).
 // st: the pair's entries staged in shared memory, entry i = degree m+i holds
 // (c^l_mn, c^l_nm) in reals 8i..8i+3 and its recurrence coefficients in
-// 8i+4..8i+7.  pc[k] = cos(b/2)^k, ps[k] = sin(b/2)^k of the candidate.
-template <typename T, bool FULL>
-__device__ __forceinline__ void pair_sum(const T *st, T K, int m, int n, int L, T x, T s,
-                                         const T *pc, const T *ps, T *A) {
+// 8i+4..8i+7.  pc[c][k] = cos(b/2)^k, ps[c][k] = sin(b/2)^k of candidate c.
+// A[c]: sum_l c^l_mn {d, d', d''} and sum_l c^l_nm {d, d', d''} (complex).
+template <typename T, bool FULL, int NC>
+__device__ __forceinline__ void pair_sum(const T *st, T K, int m, int n, int L, const T *x,
+                                         const T *s, const T *const *pc, const T *const *ps,
+                                         T (*A)[12]) {
   // seed at l = m: d = sigma K ch^a sh^b, a = m+n, b = m-n, sigma = (-1)^b
   const int a = m + n, bq = m - n;
   const T gK = ((bq & 1) ? -K : K);
-  T d0 = gK * pc[a] * ps[bq], d1 = 0, d2 = 0;
-  if (FULL) {
-    // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2; the
-    // second derivative differentiates once more.  Terms with a zero
-    // coefficient are skipped, so no negative power is read.
-    T t1 = bq >= 1 ? T(bq) * pc[a + 1] * ps[bq - 1] : T(0);
-    T t2 = a >= 1 ? T(a) * pc[a - 1] * ps[bq + 1] : T(0);
-    d1 = gK * T(0.5) * (t1 - t2);
-    T u1 = bq >= 2 ? T(bq * (bq - 1)) * pc[a + 2] * ps[bq - 2] : T(0);
-    T u2 = T(bq * (a + 1) + a * (bq + 1)) * pc[a] * ps[bq];
-    T u3 = a >= 2 ? T(a * (a - 1)) * pc[a - 2] * ps[bq + 2] : T(0);
-    d2 = gK * T(0.25) * (u1 - u2 + u3);
+  T d0[NC], d1[NC], d2[NC], p0[NC], p1[NC], p2[NC], ac[NC][12];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    d0[c] = gK * pc[c][a] * ps[c][bq];
+    d1[c] = 0; d2[c] = 0;
+    if (FULL) {
+      // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2; the
+      // second derivative differentiates once more.  Terms with a zero
+      // coefficient are skipped, so no negative power is read.
+      T t1 = bq >= 1 ? T(bq) * pc[c][a + 1] * ps[c][bq - 1] : T(0);
+      T t2 = a >= 1 ? T(a) * pc[c][a - 1] * ps[c][bq + 1] : T(0);
+      d1[c] = gK * T(0.5) * (t1 - t2);
+      T u1 = bq >= 2 ? T(bq * (bq - 1)) * pc[c][a + 2] * ps[c][bq - 2] : T(0);
+      T u2 = T(bq * (a + 1) + a * (bq + 1)) * pc[c][a] * ps[c][bq];
+      T u3 = a >= 2 ? T(a * (a - 1)) * pc[c][a - 2] * ps[c][bq + 2] : T(0);
+      d2[c] = gK * T(0.25) * (u1 - u2 + u3);
+    }
+    p0[c] = 0; p1[c] = 0; p2[c] = 0;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) ac[c][q] = 0;
   }
-  T p0 = 0, p1 = 0, p2 = 0;  // previous-degree values
-  T a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
-  T b0r = 0, b0i = 0, b1r = 0, b1i = 0, b2r = 0, b2i = 0;
   const int last = L - m;  // entries 0..last; the recurrence runs for 0..last-1
+  if constexpr (sizeof(T) == 4 && NC == 2) {
+    // Packed path: both candidates in float2 registers, one FFMA2 per pair of
+    // operations.  The sign of each subtracted term is moved into a negated
+    // operand, which is exact, so the results equal the scalar path's.
+    float2 D0 = make_float2(d0[0], d0[1]), D1 = make_float2(d1[0], d1[1]);
+    float2 D2 = make_float2(d2[0], d2[1]);
+    float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
+    const float2 X = make_float2(x[0], x[1]), Sn = make_float2(-s[0], -s[1]);
+    float2 Z[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) Z[q] = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int i = 0; i < last; ++i) {
+    for (int i = 0; i <= last; ++i) {
+      Quad<T> e, r;
+      e.load(st + 8 * i);
+      r.load(st + 8 * i + 4);
+      const float2 Cr = make_float2(e.x(), e.x()), Ci = make_float2(e.y(), e.y());
+      const float2 Dr = make_float2(e.z(), e.z()), Di = make_float2(e.w(), e.w());
+      Z[0] = __ffma2_rn(Cr, D0, Z[0]); Z[1] = __ffma2_rn(Ci, D0, Z[1]);
+      Z[2] = __ffma2_rn(Dr, D0, Z[2]); Z[3] = __ffma2_rn(Di, D0, Z[3]);
+      if (FULL) {
+        Z[4] = __ffma2_rn(Cr, D1, Z[4]); Z[5] = __ffma2_rn(Ci, D1, Z[5]);
+        Z[6] = __ffma2_rn(Dr, D1, Z[6]); Z[7] = __ffma2_rn(Di, D1, Z[7]);
+        Z[8] = __ffma2_rn(Cr, D2, Z[8]); Z[9] = __ffma2_rn(Ci, D2, Z[9]);
+        Z[10] = __ffma2_rn(Dr, D2, Z[10]); Z[11] = __ffma2_rn(Di, D2, Z[11]);
+      }
+      if (i < last) {
+        const float2 Ca = make_float2(r.x(), r.x()), nCb = make_float2(-r.y(), -r.y());
+        const float2 nCe = make_float2(-r.z(), -r.z());
+        const float2 t = __ffma2_rn(Ca, X, nCb);                      // a x - b
+        const float2 N0 = __ffma2_rn(t, D0, __fmul2_rn(nCe, P0));     // t d - e p
+        if (FULL) {
+          const float2 nAs = __fmul2_rn(Ca, Sn);                      // -a s
+          // t d' - (a s d + e p')
+          const float2 N1 = __ffma2_rn(t, D1, __ffma2_rn(nAs, D0, __fmul2_rn(nCe, P1)));
+          // t d'' - (2 a s d' + a x d + e p'')
+          const float2 nAx = make_float2(-r.x() * x[0], -r.x() * x[1]);
+          const float2 N2 = __ffma2_rn(
+              t, D2, __ffma2_rn(__fadd2_rn(nAs, nAs), D1, __ffma2_rn(nAx, D0, __fmul2_rn(nCe, P2))));
+          P1 = D1; D1 = N1;
+          P2 = D2; D2 = N2;
+        }
+        P0 = D0; D0 = N0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+      if (FULL || q < 4) { A[0][q] = Z[q].x; A[1][q] = Z[q].y; }
+    return;
+  }
+#pragma unroll 2
+  for (int i = 0; i <= last; ++i) {
     Quad<T> e, r;
     e.load(st + 8 * i);
     r.load(st + 8 * i + 4);
-    T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
-    a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
-    b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
-    if (FULL) {
-      a1r = fma(cr, d1, a1r); a1i = fma(ci, d1, a1i);
-      b1r = fma(dr, d1, b1r); b1i = fma(di, d1, b1i);
-      a2r = fma(cr, d2, a2r); a2i = fma(ci, d2, a2i);
-      b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
-    }
-    T ca = r.x(), cb = r.y(), ce = r.z();
-    T t = fma(ca, x, -cb);
-    T n0 = fma(t, d0, -ce * p0);
-    if (FULL) {
-      T as = ca * s;
-      T n1 = fma(t, d1, -fma(as, d0, ce * p1));
-      T n2 = fma(t, d2, -fma(as + as, d1, fma(ca * x, d0, ce * p2)));
-      p1 = d1; d1 = n1;
-      p2 = d2; d2 = n2;
-    }
-    p0 = d0; d0 = n0;
-  }
-  {
-    Quad<T> e;
-    e.load(st + 8 * last);
-    T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
-    a0r = fma(cr, d0, a0r); a0i = fma(ci, d0, a0i);
-    b0r = fma(dr, d0, b0r); b0i = fma(di, d0, b0i);
-    if (FULL) {
-      a1r = fma(cr, d1, a1r); a1i = fma(ci, d1, a1i);
-      b1r = fma(dr, d1, b1r); b1i = fma(di, d1, b1i);
-      a2r = fma(cr, d2, a2r); a2i = fma(ci, d2, a2i);
-      b2r = fma(dr, d2, b2r); b2i = fma(di, d2, b2i);
+    const T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
+    const T ca = r.x(), cb = r.y(), ce = r.z();
+    const bool step = i < last;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      ac[c][0] = fma(cr, d0[c], ac[c][0]); ac[c][1] = fma(ci, d0[c], ac[c][1]);
+      ac[c][2] = fma(dr, d0[c], ac[c][2]); ac[c][3] = fma(di, d0[c], ac[c][3]);
+      if (FULL) {
+        ac[c][4] = fma(cr, d1[c], ac[c][4]); ac[c][5] = fma(ci, d1[c], ac[c][5]);
+        ac[c][6] = fma(dr, d1[c], ac[c][6]); ac[c][7] = fma(di, d1[c], ac[c][7]);
+        ac[c][8] = fma(cr, d2[c], ac[c][8]); ac[c][9] = fma(ci, d2[c], ac[c][9]);
+        ac[c][10] = fma(dr, d2[c], ac[c][10]); ac[c][11] = fma(di, d2[c], ac[c][11]);
+      }
+      if (step) {
+        T t = fma(ca, x[c], -cb);
+        T n0 = fma(t, d0[c], -ce * p0[c]);
+        if (FULL) {
+          T as = ca * s[c];
+          T n1 = fma(t, d1[c], -fma(as, d0[c], ce * p1[c]));
+          T n2 = fma(t, d2[c], -fma(as + as, d1[c], fma(ca * x[c], d0[c], ce * p2[c])));
+          p1[c] = d1[c]; d1[c] = n1;
+          p2[c] = d2[c]; d2[c] = n2;
+        }
+        p0[c] = d0[c]; d0[c] = n0;
+      }
     }
   }
-  A[0] = a0r; A[1] = a0i; A[2] = b0r; A[3] = b0i;
-  if (FULL) {
-    A[4] = a1r; A[5] = a1i; A[6] = b1r; A[7] = b1i;
-    A[8] = a2r; A[9] = a2i; A[10] = b2r; A[11] = b2i;
-  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+      if (FULL || q < 4) A[c][q] = ac[c][q];
 }
 
 template <typename T, bool FULL>
@@ -200,7 +251,7 @@ __device__ __forceinline__ void add_image(T *acc, T w, int a, int b, T zr0, T zi
 
 // Evaluates C (and grad, Hessian when FULL) at pts[p] for the candidates with
 // need[p] != 0; results in res[p][0..9] (FP64).  Called by the whole CTA.
-template <typename T, bool FULL>
+template <typename T, bool FULL, int NC>
 __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
                          const int *__restrict__ pair_off, const T *__restrict__ rcoef,
                          const T *__restrict__ seedK, const double *pts, const int *need,
@@ -251,14 +302,23 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   const int slot = warp * spw + sub;
   const int nslots = NEWTON_WARPS * spw;
   const unsigned submask = cpw == 32 ? 0xffffffffu : (((1u << cpw) - 1u) << (sub * cpw));
-  const bool act = p < P && need[p];
-  T acc[10];
+  // lane carries candidates p, p + cpw, ..., p + (NC-1) cpw
+  bool actc[NC];
+  bool act = false;
+  T xs[NC], ss[NC], acc[NC][10];
+  const T *eap[NC], *egp[NC], *pcp[NC], *psp[NC];
 #pragma unroll
-  for (int i = 0; i < 10; ++i) acc[i] = 0;
-  T x = 0, s = 0;
-  const T *eap = ea + 2 * (long)p * W, *egp = eg + 2 * (long)p * W;
-  const T *pcp = pw + (2 * p) * NPW, *psp = pw + (2 * p + 1) * NPW;
-  if (act) { x = evp[8 * p]; s = evp[8 * p + 1]; }
+  for (int c = 0; c < NC; ++c) {
+    const int pc = p + c * cpw;
+    actc[c] = pc < P && need[pc];
+    act = act || actc[c];
+    const int pcc = pc < P ? pc : 0;
+    xs[c] = evp[8 * pcc]; ss[c] = evp[8 * pcc + 1];
+    eap[c] = ea + 2 * (long)pcc * W; egp[c] = eg + 2 * (long)pcc * W;
+    pcp[c] = pw + (2 * pcc) * NPW; psp[c] = pw + (2 * pcc + 1) * NPW;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc[c][i] = 0;
+  }
   // Each sub-slot walks order pairs q = slot, slot + nslots, ...; the next
   // pair's entries are copied into the other half of the slot's shared
   // buffer while the current pair is processed.
@@ -284,34 +344,39 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
     __syncwarp(submask);
     if (act) {
       int m = isqrt_floor(q), n = q - m * m - m;
-      T Acc[12];
+      T Acc[NC][12];
       const T *st = stg + cur * (BUFE + 1) * 8;
-      pair_sum<T, FULL>(st, st[8 * BUFE], m, n, L, x, s, pcp, psp, Acc);
-      // image (m, n) and its negation
-      {
-        T er = eap[2 * (m + L)] * egp[2 * (n + L)] - eap[2 * (m + L) + 1] * egp[2 * (n + L) + 1];
-        T ei = eap[2 * (m + L)] * egp[2 * (n + L) + 1] + eap[2 * (m + L) + 1] * egp[2 * (n + L)];
-        T w = q == 0 ? T(1) : T(2);
-        T zr0 = Acc[0] * er - Acc[1] * ei, zi0 = Acc[0] * ei + Acc[1] * er;
-        T zr1 = 0, zi1 = 0, zr2 = 0;
-        if (FULL) {
-          zr1 = Acc[4] * er - Acc[5] * ei; zi1 = Acc[4] * ei + Acc[5] * er;
-          zr2 = Acc[8] * er - Acc[9] * ei;
+      pair_sum<T, FULL, NC>(st, st[8 * BUFE], m, n, L, xs, ss, pcp, psp, Acc);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (!actc[c]) continue;
+        const T *Ac = Acc[c];
+        // image (m, n) and its negation
+        {
+          T er = eap[c][2 * (m + L)] * egp[c][2 * (n + L)] - eap[c][2 * (m + L) + 1] * egp[c][2 * (n + L) + 1];
+          T ei = eap[c][2 * (m + L)] * egp[c][2 * (n + L) + 1] + eap[c][2 * (m + L) + 1] * egp[c][2 * (n + L)];
+          T w = q == 0 ? T(1) : T(2);
+          T zr0 = Ac[0] * er - Ac[1] * ei, zi0 = Ac[0] * ei + Ac[1] * er;
+          T zr1 = 0, zi1 = 0, zr2 = 0;
+          if (FULL) {
+            zr1 = Ac[4] * er - Ac[5] * ei; zi1 = Ac[4] * ei + Ac[5] * er;
+            zr2 = Ac[8] * er - Ac[9] * ei;
+          }
+          add_image<T, FULL>(acc[c], w, m, n, zr0, zi0, zr1, zi1, zr2);
         }
-        add_image<T, FULL>(acc, w, m, n, zr0, zi0, zr1, zi1, zr2);
-      }
-      if (n != m && n != -m) {
-        // image (n, m): c^l_nm d^l_nm e^{i(n a + m g)}, d^l_nm = (-1)^{m-n} d^l_mn
-        T sg = ((m - n) & 1) ? T(-2) : T(2);
-        T er = eap[2 * (n + L)] * egp[2 * (m + L)] - eap[2 * (n + L) + 1] * egp[2 * (m + L) + 1];
-        T ei = eap[2 * (n + L)] * egp[2 * (m + L) + 1] + eap[2 * (n + L) + 1] * egp[2 * (m + L)];
-        T zr0 = Acc[2] * er - Acc[3] * ei, zi0 = Acc[2] * ei + Acc[3] * er;
-        T zr1 = 0, zi1 = 0, zr2 = 0;
-        if (FULL) {
-          zr1 = Acc[6] * er - Acc[7] * ei; zi1 = Acc[6] * ei + Acc[7] * er;
-          zr2 = Acc[10] * er - Acc[11] * ei;
+        if (n != m && n != -m) {
+          // image (n, m): c^l_nm d^l_nm e^{i(n a + m g)}, d^l_nm = (-1)^{m-n} d^l_mn
+          T sg = ((m - n) & 1) ? T(-2) : T(2);
+          T er = eap[c][2 * (n + L)] * egp[c][2 * (m + L)] - eap[c][2 * (n + L) + 1] * egp[c][2 * (m + L) + 1];
+          T ei = eap[c][2 * (n + L)] * egp[c][2 * (m + L) + 1] + eap[c][2 * (n + L) + 1] * egp[c][2 * (m + L)];
+          T zr0 = Ac[2] * er - Ac[3] * ei, zi0 = Ac[2] * ei + Ac[3] * er;
+          T zr1 = 0, zi1 = 0, zr2 = 0;
+          if (FULL) {
+            zr1 = Ac[6] * er - Ac[7] * ei; zi1 = Ac[6] * ei + Ac[7] * er;
+            zr2 = Ac[10] * er - Ac[11] * ei;
+          }
+          add_image<T, FULL>(acc[c], sg, n, m, zr0, zi0, zr1, zi1, zr2);
         }
-        add_image<T, FULL>(acc, sg, n, m, zr0, zi0, zr1, zi1, zr2);
       }
     }
     __syncwarp(submask);
@@ -323,10 +388,17 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   const int nq = FULL ? 10 : 1;
   for (int o = cpw; o < 32; o <<= 1)
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
-      if (i < nq) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-  if (lane < cpw && p < P)
-    for (int i = 0; i < nq; ++i) sm.red[(warp * P + p) * 10 + i] = (double)acc[i];
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int i = 0; i < 10; ++i)
+        if (i < nq) acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], o);
+  if (lane < cpw)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int pc = p + c * cpw;
+      if (pc < P)
+        for (int i = 0; i < nq; ++i) sm.red[(warp * P + pc) * 10 + i] = (double)acc[c][i];
+    }
   __syncthreads();
   for (int idx = tid; idx < P * nq; idx += blockDim.x) {
     int pp = idx / nq, i = idx - pp * nq;
@@ -427,8 +499,8 @@ __device__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) 
   sm.state[tid] = ST_TRIAL;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 2 : 3)
+template <typename T, int NC>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 2 : (NC == 1 ? 3 : 2))
 k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__restrict__ rcoef,
          const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
          double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
@@ -488,7 +560,7 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
     if (!__syncthreads_or(want)) break;
     if (tid == 0)
       for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
-    evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
+    evaluate<T, true, NC>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
     if (tid < P && need[tid]) {
       sm.steps[tid] = 0;
       start_step(tid, L, A, sm);
@@ -504,8 +576,8 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
       const bool full = __syncthreads_or(wf);
       if (tid == 0)
         for (int q = 0; q < P; ++q) (full ? work_full : work_val) += need[q] ? steps_L : 0;
-      if (full) evaluate<T, true>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
-      else evaluate<T, false>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+      if (full) evaluate<T, true, NC>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+      else evaluate<T, false, NC>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
       if (tid < P && need[tid]) {
         double Ct = sm.res[10 * tid];
         if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
@@ -549,15 +621,20 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   }
 }
 
-size_t newton_smem_bytes(const Plan &p, size_t tsize) {
+// Lanes per warp sub-slot: enough that each lane carries at most NC candidates.
+static int newton_cpw(int P, int NC) {
+  int per = (P + NC - 1) / NC, cpw = 1;
+  while (cpw < per) cpw <<= 1;
+  return cpw;
+}
+
+size_t newton_smem_bytes(const Plan &p, size_t tsize, int NC) {
   size_t P = p.P, W = 2 * p.LJ + 1;
   size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
   bytes += tsize * (8 * P + 4 * P * W + 2 * P * (2 * (size_t)p.LJ + 3)) + 32;
-  int cpw = 1;
-  while (cpw < p.P) cpw <<= 1;
-  size_t slots = (size_t)NEWTON_WARPS * (32 / cpw);
+  size_t slots = (size_t)NEWTON_WARPS * (32 / newton_cpw(p.P, NC));
   bytes += tsize * slots * 2 * (p.LJ + 2) * 8;
   return bytes;
 }
@@ -566,20 +643,21 @@ template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  // FP32 plans carry two candidates per lane (shared loads, two independent
+  // recurrence chains); FP64 plans one (register pressure)
+  constexpr int NC = sizeof(T) == 4 ? 2 : 1;
   NewtonArgs A;
   A.LJ = p.LJ; A.nlev = p.nlev; A.M = p.M; A.P = p.P;
-  int cpw = 1;
-  while (cpw < p.P) cpw <<= 1;
-  A.cpw = cpw;
+  A.cpw = newton_cpw(p.P, NC);
   for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
   A.tol = p.step_tol;
   A.acc_tol = p.accept_tol;
   A.nc = p.nc;
-  size_t smem = newton_smem_bytes(p, sizeof(T));
-  cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_newton<T><<<B, NEWTON_THREADS, smem, st>>>(c, p.pair_off, (const T *)p.rcoef,
-                                               (const T *)p.seedK, A, n_cand, euler, score, cflags,
-                                               work);
+  size_t smem = newton_smem_bytes(p, sizeof(T), NC);
+  cudaFuncSetAttribute(k_newton<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_newton<T, NC><<<B, NEWTON_THREADS, smem, st>>>(c, p.pair_off, (const T *)p.rcoef,
+                                                   (const T *)p.seedK, A, n_cand, euler, score,
+                                                   cflags, work);
   return cudaGetLastError();
 }
 
