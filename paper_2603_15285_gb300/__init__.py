@@ -337,13 +337,35 @@ def matcha_align_host(plan: Plan, particles: np.ndarray, templates: np.ndarray, 
 
 
 def corr_layout(L: int):
-    """(m, n, l) of every correlation entry in the library's pair layout."""
+    """(m, n, l) of every (pair slot, degree) row of the library's grouped
+    correlation layout, in the row order of ``corr_pairs``.
+
+    The pairs (m, n), m >= |n|, of one m are grouped two at a time
+    (n = 2j - m and 2j - m + 1, j = 0..m); the second slot of each m's last
+    group is empty and is listed with n = m + 1 (its coefficients are zero).
+    """
     rows = []
     for m in range(L + 1):
-        for n in range(-m, m + 1):
+        for j in range(m + 1):
+            na = 2 * j - m
             for l in range(m, L + 1):
-                rows.append((m, n, l))
+                rows.append((m, na, l))
+                rows.append((m, na + 1, l))
     return np.array(rows, dtype=np.int64)
+
+
+def corr_pairs(c):
+    """Rows (c^l_mn, c^l_nm) of a correlation buffer [..., corr_entries, 2, 2].
+
+    The library interleaves the two partners of a group component by
+    component (8 reals per group and degree); this returns the buffer as
+    [..., corr_entries, 2, 2] = (row, c_mn | c_nm, re | im) with rows in
+    ``corr_layout`` order.  Works on numpy arrays and torch tensors.
+    """
+    lead, n = tuple(c.shape[:-3]), c.shape[-3]
+    g = c.reshape(lead + (n // 2, 4, 2))                 # [group, l][component][slot]
+    g = g.transpose(-1, -2) if hasattr(g, "is_cuda") else np.swapaxes(g, -1, -2)
+    return g.reshape(lead + (n, 2, 2))
 
 
 def plan_for_workload(w, precision: int = FP64, **kw) -> Plan:

@@ -2,8 +2,9 @@
 // quadrature in place of the ball-harmonic radial index:
 //   c^l_{mn} = sum_s w_s f_lm(r_s) conj(h_ln(r_s)).
 // Negative orders come from f_{l,-m} = (-1)^m conj(f_lm) (real volumes).
-// Output layout: for each order pair (m, n), m >= |n|, the entries l = m..L_J
-// hold (c^l_{mn}, c^l_{nm}).
+// Output layout: the grouped layout of the plan (pairs (m, n), m >= |n|, taken
+// two at a time with equal m, components of the two partners interleaved);
+// each (pair, l), l = m..L_J, holds (c^l_{mn}, c^l_{nm}).
 #include "internal.cuh"
 
 namespace matcha {
@@ -28,7 +29,7 @@ __device__ __forceinline__ void coef_at(const T *__restrict__ f, int nlm, int s,
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, long h_stride,
-                const double *__restrict__ wrad, const int *__restrict__ pair_off, long nc,
+                const double *__restrict__ wrad, const int *__restrict__ pair_base, long nc,
                 T *__restrict__ c) {
   const long b = blockIdx.y;
   const int nlm = (L + 1) * (L + 2) / 2;
@@ -72,8 +73,9 @@ k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, 
         r2 = fma(fnr, hmr, fma(fni, hmi, r2));
         i2 = fma(fni, hmr, fma(-fnr, hmi, i2));
       }
-      T *o = cb + 4L * (pair_off[q] + l - m);
-      o[0] = r1; o[1] = i1; o[2] = r2; o[3] = i2;
+      T *o = cb + pair_base[q] + 8L * (l - m);
+      o[0] = r1; o[2] = i1; o[4] = r2; o[6] = i2;
+      if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }  // empty partner
     }
     __syncthreads();
   }
@@ -90,7 +92,7 @@ cudaError_t launch_correlate(const Plan &p, const T *f, const T *h, int B, int h
     attr[sizeof(T) == 8] = true;
   }
   k_correlate_deg<T><<<dim3(p.LJ / 2 + 1, B), 256, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad,
-                                                              p.pair_off, p.nc, c);
+                                                              p.pair_base, p.nc, c);
   return cudaGetLastError();
 }
 

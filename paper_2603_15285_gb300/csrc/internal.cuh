@@ -15,8 +15,9 @@ struct Plan {
   double R, step_tol, accept_tol;
   bool fp64;
   int nt, np, nlm, npairs, npairs0, ns;
-  long nc;   // (pair, l) entries per particle, l <= L_J
-  long nc0;  // (pair, l) entries with m <= L0 and l <= L0 (SOFFT layout)
+  int ngroups;  // partner groups of the correlation layout, (L_J+1)(L_J+2)/2
+  long nc;      // pair slots x degrees per particle (dummy halves included), 4 reals each
+  long nc0;     // (pair, l) entries with m <= L0 and l <= L0 (SOFFT layout)
   // device tables (one allocation)
   void *base = nullptr;
   double *rs, *wrad, *xj, *wj;  // S, S, nt, nt (FP64 always)
@@ -24,14 +25,12 @@ struct Plan {
   void *phi_cs;                 // real [np][2]: cos, sin (2 pi k / n_phi)
   void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
-  void *rcoef;                  // real [nc][4]: (a, b, e, 0) of the step l -> l+1
-  void *seedK;                  // real [npairs][4]: (sqrt(binom(2m, m+n)), 0, 0, 0)
+  void *rcoef;                  // real, grouped layout: (a, -b, -e, 0) of the step l -> l+1
+  void *seedK;                  // real [ngroups][4]: (sqrt(binom(2m, m+n)) of both halves, 0, 0)
   void *dft_cs;                 // real [2][np/2-1][Mp]: cos, sin (2 pi m k / n_phi), k = 1..np/2-1
   int Mp;                       // orders padded to a multiple of 4
-  int *pair_off;                // [npairs] entry offset of pair q in the L_J layout
-  int *pair_off0;               // [npairs0] entry offset of pair q in the L0 layout
-  // host copies of the layout
-  int *h_pair_off = nullptr;
+  int *pair_base;               // [npairs] first real of pair q in the grouped L_J layout
+  int *pair_off0;               // [npairs0] entry offset of pair q in the L0 (SOFFT) layout
   // copy stream and events of matcha_align_host (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev[9] = {};
@@ -39,14 +38,35 @@ struct Plan {
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-// Host-side pair layout: off(m, n) = sum_{m'<m} (2m'+1)(L-m'+1) + (n+m)(L-m+1).
+// Grouped correlation layout.  The order pairs (m, n), m >= |n|, of one m are
+// taken two at a time: group g = m(m+1)/2 + j (j = 0..m) holds the partners
+// n_a = 2j - m and n_b = n_a + 1 (half 0 and half 1); for j = m the second
+// half is empty (n_b = m + 1 does not exist) and holds zeros.  Group g covers
+// the degrees l = m..L, and each (group, l) is 8 reals with the two halves
+// interleaved: real 2k + h is component k of half h, k = 0..3 being
+// (Re, Im) of c^l_{mn} and (Re, Im) of c^l_{nm}.  Interleaving puts the same
+// component of both partners side by side, so one paired (2-wide) operation
+// advances both.
+inline long group_offset_host(int m, int j, int L) {  // in (group, l) entries
+  long o = 0;
+  for (int mm = 0; mm < m; ++mm) o += (long)(mm + 1) * (L - mm + 1);
+  return o + (long)j * (L - m + 1);
+}
+inline long group_entries_host(int L) { return group_offset_host(L + 1, 0, L); }
+// first real of pair (m, n) in the grouped layout of bandwidth L
+inline long pair_base_host(int m, int n, int L) {
+  int j = (n + m) >> 1, h = (n + m) & 1;
+  return 8 * group_offset_host(m, j, L) + h;
+}
+// Ungrouped layout of the SOFFT kernels' staged copy and of soft_d:
+// off(m, n) = sum_{m'<m} (2m'+1)(L-m'+1) + (n+m)(L-m+1) entries.
 inline long pair_offset_host(int m, int n, int L) {
   long o = 0;
   for (int mm = 0; mm < m; ++mm) o += (long)(2 * mm + 1) * (L - mm + 1);
   return o + (long)(n + m) * (L - m + 1);
 }
 inline long pair_entries_host(int L) {  // sum_{m<=L} (2m+1)(L-m+1)
-  return pair_offset_host(L + 1, -(L + 1), L) ;
+  return pair_offset_host(L + 1, -(L + 1), L);
 }
 
 // Table builders (plan_tables.cu).
@@ -64,6 +84,7 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
 template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st);
+bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
                                 const double *cand_euler, const double *cand_score,
                                 const int *cand_flags, double *euler, double *R, double *score,
@@ -90,6 +111,14 @@ __device__ __forceinline__ int isqrt_floor(int q) {
   int m = (int)sqrtf((float)q);
   while (m * m > q) --m;
   while ((m + 1) * (m + 1) <= q) ++m;
+  return m;
+}
+
+// Largest m with m(m+1)/2 <= g (the order m of partner group g).
+__device__ __forceinline__ int tri_floor(int g) {
+  int m = (int)((sqrtf(8.0f * (float)g + 1.0f) - 1.0f) * 0.5f);
+  while (m * (m + 1) / 2 > g) --m;
+  while ((m + 1) * (m + 2) / 2 <= g) ++m;
   return m;
 }
 

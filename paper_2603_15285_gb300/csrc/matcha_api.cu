@@ -117,13 +117,23 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->npairs0 = (p->L0 + 1) * (p->L0 + 1);
   p->ns = 2 * p->K * (p->L0 + 1);
   p->Mp = (p->LJ + 1 + 3) / 4 * 4;
-  p->nc = pair_entries_host(p->LJ);
+  p->ngroups = (p->LJ + 1) * (p->LJ + 2) / 2;
+  p->nc = 2 * group_entries_host(p->LJ);
   p->nc0 = pair_entries_host(p->L0);
-  std::vector<int> off(p->npairs), off0(p->npairs0);
+  if (!newton_fits(*p)) {
+    char msg[160];
+    snprintf(msg, sizeof(msg),
+             "plan: the refinement kernel's shared-memory tables do not fit for P_max = %d, "
+             "L_J = %d in this precision", p->P, p->LJ);
+    delete p;
+    set_error_text(msg);
+    return MATCHA_ERR_UNSUPPORTED;
+  }
+  std::vector<int> base(p->npairs), off0(p->npairs0);
   for (int m = 0; m <= p->LJ; ++m)
     for (int n = -m; n <= m; ++n) {
       int q = m * m + n + m;
-      off[q] = (int)pair_offset_host(m, n, p->LJ);
+      base[q] = (int)pair_base_host(m, n, p->LJ);
       if (m <= p->L0) off0[q] = (int)pair_offset_host(m, n, p->L0);
     }
   size_t rs = real_size(*p);
@@ -131,7 +141,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   auto add = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes); return o; };
   size_t o_rs = add(8 * p->S), o_w = add(8 * p->S), o_x = add(8 * p->nt), o_wj = add(8 * p->nt);
   size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
-  size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->npairs);
+  size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->ngroups);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
   size_t o_dcs = add(rs * 2 * (size_t)(p->np / 2 - 1) * p->Mp);
   cudaError_t e = cudaMalloc(&p->base, sz);
@@ -141,16 +151,13 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->xj = (double *)(b + o_x); p->wj = (double *)(b + o_wj);
   p->ptab = b + o_pt; p->phi_cs = b + o_phi; p->soft_tw = b + o_tw; p->soft_d = b + o_sd;
   p->rcoef = b + o_rc; p->seedK = b + o_K;
-  p->pair_off = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
+  p->pair_base = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
   p->dft_cs = b + o_dcs;
-  p->h_pair_off = new int[p->npairs];
-  memcpy(p->h_pair_off, off.data(), sizeof(int) * p->npairs);
-  e = cudaMemcpy(p->pair_off, off.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = build_tables(*p, 0);
   if (e != cudaSuccess) {
     cudaFree(p->base);
-    delete[] p->h_pair_off;
     delete p;
     return fail_cuda(e, "plan tables");
   }
@@ -166,7 +173,6 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
     if (ev) cudaEventDestroy(ev);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   cudaError_t e = cudaFree(p->base);
-  delete[] p->h_pair_off;
   delete p;
   if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
   return MATCHA_OK;

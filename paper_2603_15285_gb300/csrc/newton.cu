@@ -38,7 +38,7 @@ constexpr int NEWTON_WARPS = NEWTON_THREADS / 32;
 enum { ST_RUN = 0, ST_TRIAL = 1, ST_STOP = 2, ST_DEAD = 3 };
 
 struct NewtonArgs {
-  int LJ, nlev, M, P, cpw;
+  int LJ, nlev, M, P, cpw, nslots;
   int Ls[MATCHA_MAX_LEVELS];
   double tol, acc_tol;
   long nc;
@@ -65,203 +65,293 @@ template <> __device__ __forceinline__ double tsin<double>(double x) { return si
 struct SmemLayout {
   double *th, *tr, *del, *Cc, *res, *red;
   int *state, *steps, *tries, *fl;
-  void *evp, *ea, *eg, *pw, *stage;
+  void *evp, *ea, *pw, *stage;
 };
 
 // Asynchronous global -> shared copies (no registers involved).
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// Copies one entry of four reals (16 B in FP32, 32 B in FP64).
-template <typename T>
-__device__ __forceinline__ void copy_quad(T *dst, const T *src) {
-  cp_async16(dst, src);
-  if (sizeof(T) == 8) cp_async16(dst + 2, src + 2);
+// Shared-memory addressing: the hot loops address shared memory through
+// 32-bit shared-window addresses and ld.shared, so every load is a shared
+// load with 32-bit address arithmetic.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16s(unsigned sa, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void lds1(unsigned a, float &x) {
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(x) : "r"(a));
+}
+__device__ __forceinline__ void lds1(unsigned a, double &x) {
+  asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(x) : "r"(a));
+}
+__device__ __forceinline__ void lds2(unsigned a, float2 &v) {
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a));
+}
+__device__ __forceinline__ void lds2(unsigned a, double2 &v) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(v.x), "=d"(v.y) : "r"(a));
+}
+// two pairs: 16 bytes in FP32 (one vector load), 32 bytes in FP64
+__device__ __forceinline__ void lds4(unsigned a, float2 &lo, float2 &hi) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(lo.x), "=f"(lo.y), "=f"(hi.x), "=f"(hi.y)
+               : "r"(a));
+}
+__device__ __forceinline__ void lds4(unsigned a, double2 &lo, double2 &hi) {
+  lds2(a, lo);
+  lds2(a + 16, hi);
 }
 
-// 16-byte (FP32) or 32-byte (FP64) entry of four reals.
-template <typename T> struct Quad;
-template <> struct Quad<float> {
-  float4 v;
-  __device__ __forceinline__ void load(const float *p) { v = *reinterpret_cast<const float4 *>(p); }
-  __device__ __forceinline__ float x() const { return v.x; }
-  __device__ __forceinline__ float y() const { return v.y; }
-  __device__ __forceinline__ float z() const { return v.z; }
-  __device__ __forceinline__ float w() const { return v.w; }
-};
-template <> struct Quad<double> {
-  double2 a, b;
-  __device__ __forceinline__ void load(const double *p) {
-    a = *reinterpret_cast<const double2 *>(p);
-    b = *(reinterpret_cast<const double2 *>(p) + 1);
-  }
-  __device__ __forceinline__ double x() const { return a.x; }
-  __device__ __forceinline__ double y() const { return a.y; }
-  __device__ __forceinline__ double z() const { return b.x; }
-  __device__ __forceinline__ double w() const { return b.y; }
-};
+// Two-wide values: the two halves of a partner group (pairs (m, n) and
+// (m, n+1)) advance together.  FP32 uses the packed FP32x2 instructions of the
+// sm_100 family (one FFMA2 does both halves); FP64 issues two scalar FMAs.
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using v2 = typename Vec2<T>::type;
 
-// Accumulates the contributions of one order pair for NC candidates that
-// share the pair's staged entries (one lane carries NC candidates).
-// st: the pair's entries staged in shared memory, entry i = degree m+i holds
-// (c^l_mn, c^l_nm) in reals 8i..8i+3 and its recurrence coefficients in
-// 8i+4..8i+7.  pc[c][k] = cos(b/2)^k, ps[c][k] = sin(b/2)^k of candidate c.
-// A[c]: sum_l c^l_mn {d, d', d''} and sum_l c^l_nm {d, d', d''} (complex).
-template <typename T, bool FULL, int NC>
-__device__ __forceinline__ void pair_sum(const T *st, T K, int m, int n, int L, const T *x,
-                                         const T *s, const T *const *pc, const T *const *ps,
-                                         T (*A)[12]) {
-  // seed at l = m: d = sigma K ch^a sh^b, a = m+n, b = m-n, sigma = (-1)^b
-  const int a = m + n, bq = m - n;
-  const T gK = ((bq & 1) ? -K : K);
-  T d0[NC], d1[NC], d2[NC], p0[NC], p1[NC], p2[NC], ac[NC][12];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    d0[c] = gK * pc[c][a] * ps[c][bq];
-    d1[c] = 0; d2[c] = 0;
-    if (FULL) {
-      // d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1}) / 2; the
-      // second derivative differentiates once more.  Terms with a zero
-      // coefficient are skipped, so no negative power is read.
-      T t1 = bq >= 1 ? T(bq) * pc[c][a + 1] * ps[c][bq - 1] : T(0);
-      T t2 = a >= 1 ? T(a) * pc[c][a - 1] * ps[c][bq + 1] : T(0);
-      d1[c] = gK * T(0.5) * (t1 - t2);
-      T u1 = bq >= 2 ? T(bq * (bq - 1)) * pc[c][a + 2] * ps[c][bq - 2] : T(0);
-      T u2 = T(bq * (a + 1) + a * (bq + 1)) * pc[c][a] * ps[c][bq];
-      T u3 = a >= 2 ? T(a * (a - 1)) * pc[c][a - 2] * ps[c][bq + 2] : T(0);
-      d2[c] = gK * T(0.25) * (u1 - u2 + u3);
-    }
-    p0[c] = 0; p1[c] = 0; p2[c] = 0;
-#pragma unroll
-    for (int q = 0; q < 12; ++q) ac[c][q] = 0;
-  }
-  const int last = L - m;  // entries 0..last; the recurrence runs for 0..last-1
-  if constexpr (sizeof(T) == 4 && NC == 2) {
-    // Packed path: both candidates in float2 registers, one FFMA2 per pair of
-    // operations.  The sign of each subtracted term is moved into a negated
-    // operand, which is exact, so the results equal the scalar path's.
-    float2 D0 = make_float2(d0[0], d0[1]), D1 = make_float2(d1[0], d1[1]);
-    float2 D2 = make_float2(d2[0], d2[1]);
-    float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0;
-    const float2 X = make_float2(x[0], x[1]), Sn = make_float2(-s[0], -s[1]);
-    float2 Z[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) Z[q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-    for (int i = 0; i <= last; ++i) {
-      Quad<T> e, r;
-      e.load(st + 8 * i);
-      r.load(st + 8 * i + 4);
-      const float2 Cr = make_float2(e.x(), e.x()), Ci = make_float2(e.y(), e.y());
-      const float2 Dr = make_float2(e.z(), e.z()), Di = make_float2(e.w(), e.w());
-      Z[0] = __ffma2_rn(Cr, D0, Z[0]); Z[1] = __ffma2_rn(Ci, D0, Z[1]);
-      Z[2] = __ffma2_rn(Dr, D0, Z[2]); Z[3] = __ffma2_rn(Di, D0, Z[3]);
-      if (FULL) {
-        Z[4] = __ffma2_rn(Cr, D1, Z[4]); Z[5] = __ffma2_rn(Ci, D1, Z[5]);
-        Z[6] = __ffma2_rn(Dr, D1, Z[6]); Z[7] = __ffma2_rn(Di, D1, Z[7]);
-        Z[8] = __ffma2_rn(Cr, D2, Z[8]); Z[9] = __ffma2_rn(Ci, D2, Z[9]);
-        Z[10] = __ffma2_rn(Dr, D2, Z[10]); Z[11] = __ffma2_rn(Di, D2, Z[11]);
-      }
-      if (i < last) {
-        const float2 Ca = make_float2(r.x(), r.x()), nCb = make_float2(-r.y(), -r.y());
-        const float2 nCe = make_float2(-r.z(), -r.z());
-        const float2 t = __ffma2_rn(Ca, X, nCb);                      // a x - b
-        const float2 N0 = __ffma2_rn(t, D0, __fmul2_rn(nCe, P0));     // t d - e p
-        if (FULL) {
-          const float2 nAs = __fmul2_rn(Ca, Sn);                      // -a s
-          // t d' - (a s d + e p')
-          const float2 N1 = __ffma2_rn(t, D1, __ffma2_rn(nAs, D0, __fmul2_rn(nCe, P1)));
-          // t d'' - (2 a s d' + a x d + e p'')
-          const float2 nAx = make_float2(-r.x() * x[0], -r.x() * x[1]);
-          const float2 N2 = __ffma2_rn(
-              t, D2, __ffma2_rn(__fadd2_rn(nAs, nAs), D1, __ffma2_rn(nAx, D0, __fmul2_rn(nCe, P2))));
-          P1 = D1; D1 = N1;
-          P2 = D2; D2 = N2;
-        }
-        P0 = D0; D0 = N0;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 12; ++q)
-      if (FULL || q < 4) { A[0][q] = Z[q].x; A[1][q] = Z[q].y; }
-    return;
-  }
-#pragma unroll 2
-  for (int i = 0; i <= last; ++i) {
-    Quad<T> e, r;
-    e.load(st + 8 * i);
-    r.load(st + 8 * i + 4);
-    const T cr = e.x(), ci = e.y(), dr = e.z(), di = e.w();
-    const T ca = r.x(), cb = r.y(), ce = r.z();
-    const bool step = i < last;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      ac[c][0] = fma(cr, d0[c], ac[c][0]); ac[c][1] = fma(ci, d0[c], ac[c][1]);
-      ac[c][2] = fma(dr, d0[c], ac[c][2]); ac[c][3] = fma(di, d0[c], ac[c][3]);
-      if (FULL) {
-        ac[c][4] = fma(cr, d1[c], ac[c][4]); ac[c][5] = fma(ci, d1[c], ac[c][5]);
-        ac[c][6] = fma(dr, d1[c], ac[c][6]); ac[c][7] = fma(di, d1[c], ac[c][7]);
-        ac[c][8] = fma(cr, d2[c], ac[c][8]); ac[c][9] = fma(ci, d2[c], ac[c][9]);
-        ac[c][10] = fma(dr, d2[c], ac[c][10]); ac[c][11] = fma(di, d2[c], ac[c][11]);
-      }
-      if (step) {
-        T t = fma(ca, x[c], -cb);
-        T n0 = fma(t, d0[c], -ce * p0[c]);
-        if (FULL) {
-          T as = ca * s[c];
-          T n1 = fma(t, d1[c], -fma(as, d0[c], ce * p1[c]));
-          T n2 = fma(t, d2[c], -fma(as + as, d1[c], fma(ca * x[c], d0[c], ce * p2[c])));
-          p1[c] = d1[c]; d1[c] = n1;
-          p2[c] = d2[c]; d2[c] = n2;
-        }
-        p0[c] = d0[c]; d0[c] = n0;
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int q = 0; q < 12; ++q)
-      if (FULL || q < 4) A[c][q] = ac[c][q];
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+template <typename T> __device__ __forceinline__ v2<T> vset(T x, T y);
+template <> __device__ __forceinline__ float2 vset<float>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 vset<double>(double x, double y) {
+  return make_double2(x, y);
+}
+template <typename T> __device__ __forceinline__ v2<T> vld(unsigned a0, unsigned a1) {
+  T x, y;
+  lds1(a0, x);
+  lds1(a1, y);
+  return vset<T>(x, y);
 }
 
+// Offset, in (group, l) entries of the bandwidth-LJ layout, of group (m, j):
+// sum_{m'<m} (m'+1)(LJ-m'+1) + j (LJ-m+1), the sum in closed form.
+__device__ __forceinline__ int group_offset(int m, int j, int LJ) {
+  const int t = m * (m + 1) / 2;
+  return (LJ + 2) * t - t * (2 * m + 1) / 3 + j * (LJ - m + 1);
+}
+
+struct Group {
+  int m, na, off;  // order, first partner's n, offset in (group, l) entries
+};
+__device__ __forceinline__ Group group_of(int g, int LJ) {
+  const int m = tri_floor(g), j = g - m * (m + 1) / 2;
+  return {m, 2 * j - m, group_offset(m, j, LJ)};
+}
+
+// Staging buffer of one sub-slot, per half (double buffering), in reals:
+// [4] seed norms (K_a, K_b, 0, 0), then per degree entry 16 reals: the 8 c
+// reals of the group entry, then its 8 recurrence reals (a_a, a_b, -b_a,
+// -b_b, -e_a, -e_b, 0, 0); L_J + 1 entries.
+__host__ __device__ __forceinline__ int stage_half(int LJ) { return 4 + 16 * (LJ + 1); }
+
+// Power tables: per candidate two rows (cos(b/2)^k, sin(b/2)^k) of PW_PAD
+// zeros followed by k = 0 .. 2 L_J + 3.
+constexpr int PW_PAD = 4;
+__host__ __device__ __forceinline__ int pw_row(int LJ) { return PW_PAD + 2 * LJ + 4; }
+// Phase tables: per candidate four rows (cos k a, sin k a, cos k g, sin k g)
+// for k = -L_J .. L_J + 1 (index k + L_J).
+__host__ __device__ __forceinline__ int ph_row(int LJ) { return 2 * LJ + 2; }
+
+// Seeds at l = m of both halves: d = sigma K ch^a sh^b with a = m+n,
+// b = m-n, sigma = (-1)^b; with FULL also d' and d'' (Appendix A.4 applied to
+// the closed form: d/db (ch^a sh^b) = (b ch^{a+1} sh^{b-1} - a ch^{a-1} sh^{b+1})/2).
+// The first half has a = aa, b = ba (both even, so sigma = +1); the second
+// a = aa + 1, b = ba - 1 (sigma = -1).  pc, ps: shared addresses of ch^aa,
+// sh^ba in the padded power tables; a term whose integer coefficient is zero
+// may read a zero pad, so it adds exactly 0.
 template <typename T, bool FULL>
-__device__ __forceinline__ void add_image(T *acc, T w, int a, int b, T zr0, T zi0, T zr1, T zi1,
-                                          T zr2) {
-  acc[0] += w * zr0;
+__device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, v2<T> K, int aa, int ba,
+                                           v2<T> &D0, v2<T> &D1, v2<T> &D2) {
+  constexpr unsigned z = sizeof(T);
+  T c0, c1, s0, sm1;
+  lds1(pc, c0); lds1(pc + z, c1);
+  lds1(ps, s0); lds1(ps - z, sm1);
+  const v2<T> mone = vset<T>(T(-1), T(-1));
+  const v2<T> GK = vmul(K, vset<T>(T(1), T(-1)));
+  const v2<T> pp0 = vmul(vset<T>(c0, c1), vset<T>(s0, sm1));  // ch^a sh^b
+  D0 = vmul(GK, pp0);
   if (FULL) {
-    T fa = T(a), fb = T(b);
-    acc[1] += w * (-fa * zi0);
-    acc[2] += w * zr1;
-    acc[3] += w * (-fb * zi0);
-    acc[4] += w * (-fa * fa * zr0);
-    acc[5] += w * (-fa * zi1);
-    acc[6] += w * (-fa * fb * zr0);
-    acc[7] += w * zr2;
-    acc[8] += w * (-fb * zi1);
-    acc[9] += w * (-fb * fb * zr0);
+    T c2, c3, cm1, cm2, s1, s2, sm2, sm3;
+    lds1(pc + 2 * z, c2); lds1(pc + 3 * z, c3); lds1(pc - z, cm1); lds1(pc - 2 * z, cm2);
+    lds1(ps + z, s1); lds1(ps + 2 * z, s2); lds1(ps - 2 * z, sm2); lds1(ps - 3 * z, sm3);
+    const T fa = T(aa), fb = T(ba);
+    const v2<T> A = vset<T>(fa, fa + T(1)), B = vset<T>(fb, fb - T(1));
+    const v2<T> one = vset<T>(T(1), T(1));
+    const v2<T> t1 = vmul(B, vmul(vset<T>(c1, c2), vset<T>(sm1, sm2)));
+    const v2<T> t2 = vmul(A, vmul(vset<T>(cm1, c0), vset<T>(s1, s0)));
+    D1 = vmul(vmul(GK, vset<T>(T(0.5), T(0.5))), vfma(t2, mone, t1));
+    // b(b-1) ch^{a+2} sh^{b-2} - (b(a+1) + a(b+1)) ch^a sh^b + a(a-1) ch^{a-2} sh^{b+2}
+    const v2<T> u1 = vmul(vmul(B, vadd(B, mone)), vmul(vset<T>(c2, c3), vset<T>(sm2, sm3)));
+    const v2<T> u2 = vmul(vfma(B, vadd(A, one), vmul(A, vadd(B, one))), pp0);
+    const v2<T> u3 = vmul(vmul(A, vadd(A, mone)), vmul(vset<T>(cm2, cm1), vset<T>(s2, s1)));
+    D2 = vmul(vmul(GK, vset<T>(T(0.25), T(0.25))), vfma(u2, mone, vadd(u1, u3)));
   }
+}
+
+// One staged degree entry of a partner group: c of both halves, and the
+// recurrence coefficients (a, -b, -e) of the step to the next degree.
+template <typename T> struct Coef {
+  v2<T> CR, CI, DR, DI;
+};
+template <typename T> struct Rec {
+  v2<T> A, NB, NE;
+};
+template <typename T> __device__ __forceinline__ void load_coef(unsigned a, Coef<T> &e) {
+  lds4(a, e.CR, e.CI);
+  lds4(a + 4 * sizeof(T), e.DR, e.DI);
+}
+template <typename T> __device__ __forceinline__ void load_rec(unsigned a, Rec<T> &r) {
+  lds4(a + 8 * sizeof(T), r.A, r.NB);
+  lds2(a + 12 * sizeof(T), r.NE);
+}
+// Z += c d (and c d', c d'' when FULL) for one entry.
+template <typename T, bool FULL>
+__device__ __forceinline__ void accumulate(const Coef<T> &e, const v2<T> &D0, const v2<T> &D1,
+                                           const v2<T> &D2, v2<T> (&Z)[12]) {
+  Z[0] = vfma(e.CR, D0, Z[0]); Z[1] = vfma(e.CI, D0, Z[1]);
+  Z[2] = vfma(e.DR, D0, Z[2]); Z[3] = vfma(e.DI, D0, Z[3]);
+  if (FULL) {
+    Z[4] = vfma(e.CR, D1, Z[4]); Z[5] = vfma(e.CI, D1, Z[5]);
+    Z[6] = vfma(e.DR, D1, Z[6]); Z[7] = vfma(e.DI, D1, Z[7]);
+    Z[8] = vfma(e.CR, D2, Z[8]); Z[9] = vfma(e.CI, D2, Z[9]);
+    Z[10] = vfma(e.DR, D2, Z[10]); Z[11] = vfma(e.DI, D2, Z[11]);
+  }
+}
+// One recurrence step from (d^l, d^{l-1}) = (D, P); d^{l+1} overwrites P:
+//   d^{l+1} = t d - e p,  t = a x - b,
+//   d'^{l+1} = t d' - a s d - e p',  d''^{l+1} = t d'' - 2 a s d' - a x d - e p''.
+template <typename T, bool FULL>
+__device__ __forceinline__ void step_into(const Rec<T> &r, v2<T> X, v2<T> NS, v2<T> NX,
+                                          const v2<T> &D0, const v2<T> &D1, const v2<T> &D2,
+                                          v2<T> &P0, v2<T> &P1, v2<T> &P2) {
+  const v2<T> t = vfma(r.A, X, r.NB);
+  P0 = vfma(t, D0, vmul(r.NE, P0));
+  if (FULL) {
+    const v2<T> nAs = vmul(r.A, NS);
+    P1 = vfma(t, D1, vfma(nAs, D0, vmul(r.NE, P1)));
+    const v2<T> nAx = vmul(r.A, NX);
+    P2 = vfma(t, D2, vfma(vadd(nAs, nAs), D1, vfma(nAx, D0, vmul(r.NE, P2))));
+  }
+}
+
+// Sums over l = m..m+last of one partner group for one candidate: Z[0..3] =
+// sum d (Re c_mn, Im c_mn, Re c_nm, Im c_nm), then the same with d' (Z[4..7])
+// and d'' (Z[8..11]) when FULL; each a pair over the two halves.  a: shared
+// address of the group's first staged entry (16 reals per entry).  The loop
+// takes two degrees per trip with the roles of (D, P) swapped in the second;
+// c is loaded one degree ahead of its use, the step coefficients at the start
+// of their degree.
+template <typename T, bool FULL>
+__device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> NS, v2<T> NX,
+                                          v2<T> D0, v2<T> D1, v2<T> D2, v2<T> (&Z)[12]) {
+  constexpr unsigned ES = 16 * sizeof(T);
+  const v2<T> zero = vset<T>(T(0), T(0));
+  v2<T> P0 = zero, P1 = zero, P2 = zero;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) Z[q] = zero;
+  Coef<T> e0, e1;
+  Rec<T> r;
+  load_coef(a, e0);
+  int i = 0;
+  for (; i + 2 <= last; i += 2, a += 2 * ES) {
+    load_rec(a, r);
+    load_coef(a + ES, e1);
+    accumulate<T, FULL>(e0, D0, D1, D2, Z);
+    step_into<T, FULL>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+    load_rec(a + ES, r);
+    load_coef(a + 2 * ES, e0);
+    accumulate<T, FULL>(e1, P0, P1, P2, Z);
+    step_into<T, FULL>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
+  }
+  if (i < last) {  // degrees i (with a step) and last = i + 1
+    load_rec(a, r);
+    load_coef(a + ES, e1);
+    accumulate<T, FULL>(e0, D0, D1, D2, Z);
+    step_into<T, FULL>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+    accumulate<T, FULL>(e1, P0, P1, P2, Z);
+  } else {         // degree last = i
+    accumulate<T, FULL>(e0, D0, D1, D2, Z);
+  }
+}
+
+// Adds one image of both halves to the candidate's sums.  The image has phase
+// E = e^{i(u a + v g)} and weight W; (zr0, zi0) = S0 E, (zr1, zi1) = S1 E,
+// zr2 = Re S2 E for the d, d', d'' sums S0, S1, S2.  d/da brings i u and d/dg
+// brings i v, so with AU = -W u, GV = -W v:
+//   C += W zr0, C_a += AU zi0, C_b += W zr1, C_g += GV zi0,
+//   C_aa += AU u zr0, C_ab += AU zi1, C_ag += AU v zr0, C_bb += W zr2,
+//   C_bg += GV zi1, C_gg += GV v zr0.
+template <typename T, bool FULL>
+__device__ __forceinline__ void add_image(v2<T> (&acc)[10], v2<T> W, v2<T> U, v2<T> V,
+                                          const v2<T> &ER, const v2<T> &EI, const v2<T> &NEI,
+                                          const v2<T> &S0r, const v2<T> &S0i, const v2<T> &S1r,
+                                          const v2<T> &S1i, const v2<T> &S2r, const v2<T> &S2i) {
+  const v2<T> zr0 = vfma(S0r, ER, vmul(S0i, NEI));
+  acc[0] = vfma(W, zr0, acc[0]);
+  if (FULL) {
+    const v2<T> mone = vset<T>(T(-1), T(-1));
+    const v2<T> zi0 = vfma(S0r, EI, vmul(S0i, ER));
+    const v2<T> zr1 = vfma(S1r, ER, vmul(S1i, NEI));
+    const v2<T> zi1 = vfma(S1r, EI, vmul(S1i, ER));
+    const v2<T> zr2 = vfma(S2r, ER, vmul(S2i, NEI));
+    const v2<T> NW = vmul(W, mone);
+    const v2<T> AU = vmul(NW, U), GV = vmul(NW, V);
+    acc[1] = vfma(AU, zi0, acc[1]);
+    acc[2] = vfma(W, zr1, acc[2]);
+    acc[3] = vfma(GV, zi0, acc[3]);
+    acc[4] = vfma(vmul(AU, U), zr0, acc[4]);
+    acc[5] = vfma(AU, zi1, acc[5]);
+    acc[6] = vfma(vmul(AU, V), zr0, acc[6]);
+    acc[7] = vfma(W, zr2, acc[7]);
+    acc[8] = vfma(GV, zi1, acc[8]);
+    acc[9] = vfma(vmul(GV, V), zr0, acc[9]);
+  }
+}
+
+// Phase pair E = (cos, sin) rows product: E = EA EG with EA = (ar + i ai),
+// EG = (gr + i gi) pairs; returns Re, Im and -Im.
+template <typename T>
+__device__ __forceinline__ void phase(v2<T> Ar, v2<T> Ai, v2<T> Gr, v2<T> Gi, v2<T> &ER,
+                                      v2<T> &EI, v2<T> &NEI) {
+  const v2<T> mone = vset<T>(T(-1), T(-1));
+  ER = vfma(Ar, Gr, vmul(vmul(Ai, mone), Gi));
+  EI = vfma(Ar, Gi, vmul(Ai, Gr));
+  NEI = vmul(EI, mone);
 }
 
 // Evaluates C (and grad, Hessian when FULL) at pts[p] for the candidates with
 // need[p] != 0; results in res[p][0..9] (FP64).  Called by the whole CTA.
-template <typename T, bool FULL, int NC>
-__device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
-                         const int *__restrict__ pair_off, const T *__restrict__ rcoef,
-                         const T *__restrict__ seedK, const double *pts, const int *need,
-                         SmemLayout &sm) {
-  const int P = A.P, cpw = A.cpw, W = 2 * L + 1;
+//
+// Lane layout: a warp holds 32 / cpw sub-slots of cpw lanes; lane p of a
+// sub-slot follows candidate p.  Sub-slot `slot` walks the partner groups
+// g = slot, slot + nslots, ... of bandwidth L; the next group's entries are
+// copied into the other half of the slot's buffer while the current one is
+// summed, so every shared-memory read in the l-loop is a broadcast.
+template <typename T, bool FULL>
+__device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
+                                         const T *__restrict__ rcoef, const T *__restrict__ seedK,
+                                         const double *pts, const int *need, SmemLayout &sm) {
+  constexpr unsigned z = sizeof(T);
+  const int P = A.P, cpw = A.cpw, LJ = A.LJ;
+  const int NPW = pw_row(LJ), RW = ph_row(LJ);
   T *evp = (T *)sm.evp;  // [P][8]: x, s, ch, sh, cos a, sin a, cos g, sin g
-  T *ea = (T *)sm.ea;    // [P][W][2]: e^{i m a}, m = -L..L
-  T *eg = (T *)sm.eg;
-  T *pw = (T *)sm.pw;    // [P][2][NPW]: ch^k, sh^k
-  const int NPW = 2 * A.LJ + 3;
+  T *ph = (T *)sm.ea;    // [P][4][RW]: cos k a, sin k a, cos k g, sin k g
+  T *pw = (T *)sm.pw;    // [P][2][NPW]: PW_PAD zeros, then ch^k (sh^k), k = 0..2LJ+3
   const int tid = threadIdx.x;
   if (tid < P && need[tid]) {
     T al = (T)pts[3 * tid], be = (T)pts[3 * tid + 1], ga = (T)pts[3 * tid + 2];
@@ -272,24 +362,25 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
     e[6] = tcos(ga); e[7] = tsin(ga);
   }
   __syncthreads();
-  const FastDiv dw(2 * L + 3);
-  for (int t = tid; t < 2 * P * (2 * L + 3); t += blockDim.x) {
-    int pr = dw.div(t), k = t - pr * (2 * L + 3);
+  const int npk = 2 * L + 4;  // powers k = 0..2L+3
+  const FastDiv dw(npk);
+  for (int t = tid; t < 2 * P * npk; t += blockDim.x) {
+    int pr = dw.div(t), k = t - pr * npk;
     int p = pr >> 1, which = pr & 1;
-    if (need[p]) pw[(2 * p + which) * NPW + k] = ipow_t(evp[8 * p + 2 + which], k);
+    if (need[p]) pw[pr * NPW + PW_PAD + k] = ipow_t(evp[8 * p + 2 + which], k);
   }
   if (tid < 2 * P) {
     int p = tid >> 1, which = tid & 1;
     if (need[p]) {
       T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
-      T *tab = (which ? eg : ea) + 2 * (long)p * W;
+      T *cr_ = ph + ((long)p * 4 + 2 * which) * RW + LJ, *ci_ = cr_ + RW;
       T cr = 1, ci = 0;
-      tab[2 * L] = 1; tab[2 * L + 1] = 0;
-      for (int m = 1; m <= L; ++m) {
+      cr_[0] = 1; ci_[0] = 0;
+      for (int m = 1; m <= L + 1; ++m) {
         T nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
         cr = nr; ci = ni;
-        tab[2 * (L + m)] = cr; tab[2 * (L + m) + 1] = ci;
-        tab[2 * (L - m)] = cr; tab[2 * (L - m) + 1] = -ci;
+        cr_[m] = cr; ci_[m] = ci;
+        if (m <= L) { cr_[-m] = cr; ci_[-m] = -ci; }
       }
     }
   }
@@ -300,105 +391,108 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   const int p = lane & (cpw - 1);
   const int sub = lane / cpw;
   const int slot = warp * spw + sub;
-  const int nslots = NEWTON_WARPS * spw;
+  const int nslots = A.nslots;  // sub-slots with a staging buffer (<= NEWTON_WARPS * spw)
   const unsigned submask = cpw == 32 ? 0xffffffffu : (((1u << cpw) - 1u) << (sub * cpw));
-  // lane carries candidates p, p + cpw, ..., p + (NC-1) cpw
-  bool actc[NC];
-  bool act = false;
-  T xs[NC], ss[NC], acc[NC][10];
-  const T *eap[NC], *egp[NC], *pcp[NC], *psp[NC];
+  const bool act = p < P && need[p];
+  const int pc = p < P ? p : 0;
+  const T xb = evp[8 * pc], sb = evp[8 * pc + 1];
+  const v2<T> X = vset<T>(xb, xb), NS = vset<T>(-sb, -sb), NX = vset<T>(-xb, -xb);
+  // shared addresses of this candidate's tables (index 0 of each row)
+  const unsigned pcu = smem_u32(pw + (2 * pc) * NPW + PW_PAD);
+  const unsigned psu = pcu + z * NPW;
+  const unsigned eacu = smem_u32(ph + (long)pc * 4 * RW + LJ);  // k = 0 of cos k a
+  const unsigned easu = eacu + z * RW, egcu = easu + z * RW, egsu = egcu + z * RW;
+  v2<T> acc[10];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int pc = p + c * cpw;
-    actc[c] = pc < P && need[pc];
-    act = act || actc[c];
-    const int pcc = pc < P ? pc : 0;
-    xs[c] = evp[8 * pcc]; ss[c] = evp[8 * pcc + 1];
-    eap[c] = ea + 2 * (long)pcc * W; egp[c] = eg + 2 * (long)pcc * W;
-    pcp[c] = pw + (2 * pcc) * NPW; psp[c] = pw + (2 * pcc + 1) * NPW;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) acc[c][i] = 0;
-  }
-  // Each sub-slot walks order pairs q = slot, slot + nslots, ...; the next
-  // pair's entries are copied into the other half of the slot's shared
-  // buffer while the current pair is processed.
-  const int npl = (L + 1) * (L + 1);
-  const int BUFE = A.LJ + 1;
-  T *stg = (T *)sm.stage + (long)slot * 2 * (BUFE + 1) * 8;
-  auto issue = [&](int qq, int half) {
-    int mm = isqrt_floor(qq), len = L - mm + 1, off = pair_off[qq];
-    T *dst = stg + half * (BUFE + 1) * 8;
-    for (int e = p; e < len; e += cpw) {
-      copy_quad<T>(dst + 8 * e, cb + 4L * (off + e));
-      copy_quad<T>(dst + 8 * e + 4, rcoef + 4L * (off + e));
-    }
-    if (p == 0) copy_quad<T>(dst + 8 * BUFE, seedK + 4L * qq);  // (K, 0, 0, 0)
+  for (int i = 0; i < 10; ++i) acc[i] = vset<T>(T(0), T(0));
+
+  const int ng = (L + 1) * (L + 2) / 2;
+  const unsigned HB = z * stage_half(LJ);  // bytes per half buffer
+  const unsigned stg = smem_u32(sm.stage) + (unsigned)(slot < nslots ? slot : 0) * 2 * HB;
+  // Copy duty of this lane: 16-byte chunk `part` of every entry e = e0,
+  // e0 + estep, ...; parts below CPE/2 come from c, the rest from the
+  // recurrence table.
+  constexpr int CH = 16 / (int)sizeof(T), CPE = 16 / CH;  // reals per chunk, chunks per entry
+  const int part = p % CPE, e0 = p / CPE, estep = cpw / CPE;
+  const T *srcb = (part < CPE / 2 ? cb : rcoef) + CH * (part % (CPE / 2)) + 8 * e0;
+  const unsigned dsto = z * (4 + 16 * e0 + CH * part);
+  auto issue = [&](const Group &G, int g, unsigned hb) {
+    const int len = L - G.m + 1;
+    const T *src = srcb + 8L * G.off;
+    unsigned dst = hb + dsto;
+    for (int e = e0; e < len; e += estep, src += 8 * estep, dst += 16 * z * estep)
+      cp_async16s(dst, src);
+    if (p < 4 / CH) cp_async16s(hb + 16 * p, seedK + 4L * g + CH * p);
   };
-  int cur = 0;
-  if (slot < npl) issue(slot, 0);
-  cp_async_commit();
-  for (int q = slot; q < npl; q += nslots) {
-    if (q + nslots < npl) issue(q + nslots, cur ^ 1);
+  if (slot < nslots && slot < ng) {
+    int cur = 0;
+    Group nx = group_of(slot, LJ);
+    issue(nx, slot, stg);
     cp_async_commit();
-    cp_async_wait<1>();
-    __syncwarp(submask);
-    if (act) {
-      int m = isqrt_floor(q), n = q - m * m - m;
-      T Acc[NC][12];
-      const T *st = stg + cur * (BUFE + 1) * 8;
-      pair_sum<T, FULL, NC>(st, st[8 * BUFE], m, n, L, xs, ss, pcp, psp, Acc);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (!actc[c]) continue;
-        const T *Ac = Acc[c];
-        // image (m, n) and its negation
+    for (int g = slot; g < ng; g += nslots) {
+      const Group G = nx;
+      if (g + nslots < ng) {
+        nx = group_of(g + nslots, LJ);
+        issue(nx, g + nslots, stg + (cur ^ 1) * HB);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncwarp(submask);
+      if (act) {
+        const int m = G.m, na = G.na, aa = m + na, ba = m - na;
+        const unsigned buf = stg + cur * HB;
+        v2<T> K, D0, D1, D2, Z[12];
+        lds2(buf, K);
+        D1 = D2 = vset<T>(T(0), T(0));
+        group_seed<T, FULL>(pcu + z * aa, psu + z * ba, K, aa, ba, D0, D1, D2);
+        group_sum<T, FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+        const T fm = T(m), fa = T(na);
+        const v2<T> MM = vset<T>(fm, fm), NN = vset<T>(fa, fa + T(1));
+        // image (m, n): phase e^{i(m a + n g)}, weight 1 for (0, 0) else 2
+        // (the image (-m, -n) is the conjugate); an empty half has weight 0
         {
-          T er = eap[c][2 * (m + L)] * egp[c][2 * (n + L)] - eap[c][2 * (m + L) + 1] * egp[c][2 * (n + L) + 1];
-          T ei = eap[c][2 * (m + L)] * egp[c][2 * (n + L) + 1] + eap[c][2 * (m + L) + 1] * egp[c][2 * (n + L)];
-          T w = q == 0 ? T(1) : T(2);
-          T zr0 = Ac[0] * er - Ac[1] * ei, zi0 = Ac[0] * ei + Ac[1] * er;
-          T zr1 = 0, zi1 = 0, zr2 = 0;
-          if (FULL) {
-            zr1 = Ac[4] * er - Ac[5] * ei; zi1 = Ac[4] * ei + Ac[5] * er;
-            zr2 = Ac[8] * er - Ac[9] * ei;
-          }
-          add_image<T, FULL>(acc[c], w, m, n, zr0, zi0, zr1, zi1, zr2);
+          v2<T> ER, EI, NEI;
+          T ar, ai;
+          lds1(eacu + z * m, ar);
+          lds1(easu + z * m, ai);
+          phase<T>(vset<T>(ar, ar), vset<T>(ai, ai), vld<T>(egcu + z * na, egcu + z * (na + 1)),
+                   vld<T>(egsu + z * na, egsu + z * (na + 1)), ER, EI, NEI);
+          const v2<T> Wt = vset<T>(m == 0 ? T(1) : T(2), na < m ? T(2) : T(0));
+          add_image<T, FULL>(acc, Wt, MM, NN, ER, EI, NEI, Z[0], Z[1], Z[4], Z[5], Z[8], Z[9]);
         }
-        if (n != m && n != -m) {
-          // image (n, m): c^l_nm d^l_nm e^{i(n a + m g)}, d^l_nm = (-1)^{m-n} d^l_mn
-          T sg = ((m - n) & 1) ? T(-2) : T(2);
-          T er = eap[c][2 * (n + L)] * egp[c][2 * (m + L)] - eap[c][2 * (n + L) + 1] * egp[c][2 * (m + L) + 1];
-          T ei = eap[c][2 * (n + L)] * egp[c][2 * (m + L) + 1] + eap[c][2 * (n + L) + 1] * egp[c][2 * (m + L)];
-          T zr0 = Ac[2] * er - Ac[3] * ei, zi0 = Ac[2] * ei + Ac[3] * er;
-          T zr1 = 0, zi1 = 0, zr2 = 0;
-          if (FULL) {
-            zr1 = Ac[6] * er - Ac[7] * ei; zi1 = Ac[6] * ei + Ac[7] * er;
-            zr2 = Ac[10] * er - Ac[11] * ei;
-          }
-          add_image<T, FULL>(acc[c], sg, n, m, zr0, zi0, zr1, zi1, zr2);
+        // image (n, m): c^l_nm d^l_nm e^{i(n a + m g)}, d^l_nm = (-1)^{m-n} d^l_mn
+        // (m - n even in the first half, odd in the second); absent when n = +-m
+        {
+          v2<T> ER, EI, NEI;
+          T gr, gi;
+          lds1(egcu + z * m, gr);
+          lds1(egsu + z * m, gi);
+          phase<T>(vld<T>(eacu + z * na, eacu + z * (na + 1)),
+                   vld<T>(easu + z * na, easu + z * (na + 1)), vset<T>(gr, gr), vset<T>(gi, gi),
+                   ER, EI, NEI);
+          const v2<T> Wt = vset<T>(na == m || na == -m ? T(0) : T(2), na + 1 < m ? T(-2) : T(0));
+          add_image<T, FULL>(acc, Wt, NN, MM, ER, EI, NEI, Z[2], Z[3], Z[6], Z[7], Z[10], Z[11]);
         }
       }
+      __syncwarp(submask);
+      cur ^= 1;
     }
-    __syncwarp(submask);
-    cur ^= 1;
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
-  // reduce over the sub-slots of the warp that follow the same candidate
-  // (in the working precision; the cross-warp sum below is FP64)
+  // both halves, then the sub-slots of the warp that follow the same candidate
+  // (working precision; the cross-warp sum below is FP64)
   const int nq = FULL ? 10 : 1;
+  T r[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) r[i] = acc[i].x + acc[i].y;
   for (int o = cpw; o < 32; o <<= 1)
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
+    for (int i = 0; i < 10; ++i)
+      if (i < nq) r[i] += __shfl_xor_sync(0xffffffffu, r[i], o);
+  if (lane < cpw && p < P)
 #pragma unroll
-      for (int i = 0; i < 10; ++i)
-        if (i < nq) acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], o);
-  if (lane < cpw)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int pc = p + c * cpw;
-      if (pc < P)
-        for (int i = 0; i < nq; ++i) sm.red[(warp * P + pc) * 10 + i] = (double)acc[c][i];
-    }
+    for (int i = 0; i < 10; ++i)
+      if (i < nq) sm.red[(warp * P + p) * 10 + i] = (double)r[i];
   __syncthreads();
   for (int idx = tid; idx < P * nq; idx += blockDim.x) {
     int pp = idx / nq, i = idx - pp * nq;
@@ -411,7 +505,7 @@ __device__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
   __syncthreads();
 }
 
-__device__ double mod2pi_d(double x) {
+__device__ __forceinline__ double mod2pi_d(double x) {
   const double t = 2.0 * M_PI;
   double r = x - t * floor(x / t);
   if (r >= t) r -= t;
@@ -419,7 +513,7 @@ __device__ double mod2pi_d(double x) {
   return r;
 }
 
-__device__ void wrap_d(double *v) {
+__device__ __forceinline__ void wrap_d(double *v) {
   double a = v[0], b = v[1], g = v[2];
   if (b < 0) { b = -b; a += M_PI; g += M_PI; }
   else if (b > M_PI) { b = 2.0 * M_PI - b; a += M_PI; g += M_PI; }
@@ -427,7 +521,7 @@ __device__ void wrap_d(double *v) {
 }
 
 // Newton direction from grad g and Hessian H (row-major 3x3); returns flag bits.
-__device__ int newton_dir(const double *g, const double *H, int L, double *d) {
+__device__ __forceinline__ int newton_dir(const double *g, const double *H, int L, double *d) {
   double hn = 0;
   for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
   hn = sqrt(hn);
@@ -470,7 +564,7 @@ __device__ int newton_dir(const double *g, const double *H, int L, double *d) {
 // Candidate tid has C, grad, H of its current point in res: record C, stop on
 // a non-finite value (flag bit 0), take the Newton direction, stop the level
 // when the increment is below step_tol, else prepare the first trial.
-__device__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) {
+__device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) {
   const double *r = sm.res + 10 * tid;
   double C = r[0], g[3] = {r[1], r[2], r[3]};
   double H[9] = {r[4], r[5], r[6], r[5], r[7], r[8], r[6], r[8], r[9]};
@@ -499,9 +593,9 @@ __device__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) 
   sm.state[tid] = ST_TRIAL;
 }
 
-template <typename T, int NC>
-__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 2 : (NC == 1 ? 3 : 2))
-k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__restrict__ rcoef,
+template <typename T>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
          const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
          double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
          long long *__restrict__ work) {
@@ -525,15 +619,14 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   uintptr_t u = reinterpret_cast<uintptr_t>(ip);
   u = (u + 15) & ~uintptr_t(15);
   T *tp = reinterpret_cast<T *>(u);
-  const int Wm = 2 * A.LJ + 1;
   sm.evp = tp; tp += 8 * P;
-  sm.ea = tp; tp += 2 * P * Wm;
-  sm.eg = tp; tp += 2 * P * Wm;
-  sm.pw = tp; tp += 2 * P * (2 * A.LJ + 3);
+  sm.ea = tp; tp += 4 * P * ph_row(A.LJ);  // phase rows
+  sm.pw = tp; tp += 2 * P * pw_row(A.LJ);
   tp = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(tp) + 31) & ~uintptr_t(31));
   sm.stage = tp;  // [slots][2][L_J+1][8]
 
   const int nc_b = n_cand[b];
+  for (int t = tid; t < 2 * P * pw_row(A.LJ); t += blockDim.x) ((T *)sm.pw)[t] = T(0);  // pads
   if (tid < P) {
     double *e = euler + 3 * (b * P + tid);
     sm.th[3 * tid] = e[0]; sm.th[3 * tid + 1] = e[1]; sm.th[3 * tid + 2] = e[2];
@@ -560,7 +653,7 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
     if (!__syncthreads_or(want)) break;
     if (tid == 0)
       for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
-    evaluate<T, true, NC>(A, L, cb, pair_off, rcoef, seedK, sm.th, need, sm);
+    evaluate<T, true>(A, L, cb, rcoef, seedK, sm.th, need, sm);
     if (tid < P && need[tid]) {
       sm.steps[tid] = 0;
       start_step(tid, L, A, sm);
@@ -576,8 +669,8 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
       const bool full = __syncthreads_or(wf);
       if (tid == 0)
         for (int q = 0; q < P; ++q) (full ? work_full : work_val) += need[q] ? steps_L : 0;
-      if (full) evaluate<T, true, NC>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
-      else evaluate<T, false, NC>(A, L, cb, pair_off, rcoef, seedK, sm.tr, need, sm);
+      if (full) evaluate<T, true>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
+      else evaluate<T, false>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
       if (tid < P && need[tid]) {
         double Ct = sm.res[10 * tid];
         if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
@@ -621,43 +714,48 @@ k_newton(const T *__restrict__ c, const int *__restrict__ pair_off, const T *__r
   }
 }
 
-// Lanes per warp sub-slot: enough that each lane carries at most NC candidates.
-static int newton_cpw(int P, int NC) {
-  int per = (P + NC - 1) / NC, cpw = 1;
-  while (cpw < per) cpw <<= 1;
-  return cpw;
-}
+// Lanes per warp sub-slot: one per candidate, at least 16.
+static int newton_cpw(int P) { return P <= 16 ? 16 : 32; }
 
-size_t newton_smem_bytes(const Plan &p, size_t tsize, int NC) {
-  size_t P = p.P, W = 2 * p.LJ + 1;
+// Shared memory of k_newton with `slots` staging buffers.
+static size_t newton_smem_bytes(const Plan &p, size_t tsize, int slots) {
+  size_t P = p.P;
   size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
-  bytes += tsize * (8 * P + 4 * P * W + 2 * P * (2 * (size_t)p.LJ + 3)) + 32;
-  size_t slots = (size_t)NEWTON_WARPS * (32 / newton_cpw(p.P, NC));
-  bytes += tsize * slots * 2 * (p.LJ + 2) * 8;
+  bytes += tsize * (8 * P + 4 * P * ph_row(p.LJ) + 2 * P * pw_row(p.LJ)) + 32;
+  bytes += tsize * (size_t)slots * 2 * stage_half(p.LJ);
   return bytes;
 }
+
+// Staging buffers that fit: one per sub-slot when possible, else fewer (the
+// other sub-slots then idle); 0 when even one does not fit.
+static int newton_slots(const Plan &p, size_t tsize) {
+  const size_t limit = 227 * 1024;
+  int slots = NEWTON_WARPS * (32 / newton_cpw(p.P));
+  while (slots > 0 && newton_smem_bytes(p, tsize, slots) > limit) --slots;
+  return slots;
+}
+
+bool newton_fits(const Plan &p) { return newton_slots(p, p.fp64 ? 8 : 4) > 0; }
 
 template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  // FP32 plans carry two candidates per lane (shared loads, two independent
-  // recurrence chains); FP64 plans one (register pressure)
-  constexpr int NC = sizeof(T) == 4 ? 2 : 1;
   NewtonArgs A;
   A.LJ = p.LJ; A.nlev = p.nlev; A.M = p.M; A.P = p.P;
-  A.cpw = newton_cpw(p.P, NC);
+  A.cpw = newton_cpw(p.P);
+  A.nslots = newton_slots(p, sizeof(T));
+  if (A.nslots == 0) return cudaErrorInvalidConfiguration;
   for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
   A.tol = p.step_tol;
   A.acc_tol = p.accept_tol;
   A.nc = p.nc;
-  size_t smem = newton_smem_bytes(p, sizeof(T), NC);
-  cudaFuncSetAttribute(k_newton<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_newton<T, NC><<<B, NEWTON_THREADS, smem, st>>>(c, p.pair_off, (const T *)p.rcoef,
-                                                   (const T *)p.seedK, A, n_cand, euler, score,
-                                                   cflags, work);
+  size_t smem = newton_smem_bytes(p, sizeof(T), A.nslots);
+  cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_newton<T><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK, A,
+                                               n_cand, euler, score, cflags, work);
   return cudaGetLastError();
 }
 

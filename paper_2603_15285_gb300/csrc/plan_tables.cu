@@ -83,8 +83,11 @@ __global__ void k_twiddle(int n, double *cs) {
   cs[2 * k + 1] = s;
 }
 
-// rcoef[entry] for every (pair q, l), entry = pair_off[q] + l - m.
-__global__ void k_rcoef(int L, int npairs, const int *pair_off, double *rc) {
+// Recurrence coefficients of every (pair q, l) in the grouped layout: reals
+// pair_base[q] + 8 (l - m) + {0, 2, 4, 6} = (a, -b, -e, 0) of the step
+// d^{l+1} = (a x - b) d^l - e d^{l-1}; zero at l = L.  The empty half of each
+// m's last group (partner of n = m) is zero.
+__global__ void k_rcoef(int L, int npairs, const int *pair_base, double *rc) {
   int q = blockIdx.x;
   if (q >= npairs) return;
   int m = 0;
@@ -104,22 +107,30 @@ __global__ void k_rcoef(int L, int npairs, const int *pair_off, double *rc) {
         e = l1 * q0 / (ll * q1);
       }
     }
-    double *o = rc + 4 * (long)(pair_off[q] + l - m);
-    o[0] = a; o[1] = b; o[2] = e; o[3] = 0;
+    double *o = rc + pair_base[q] + 8L * (l - m);
+    o[0] = a; o[2] = -b; o[4] = -e; o[6] = 0;
+    if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }
   }
 }
 
-__global__ void k_seedK(int npairs, double *K) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= npairs) return;
-  int m = 0;
-  while ((m + 1) * (m + 1) <= q) ++m;
-  int n = q - m * m - m;
-  // C(2m, m+n) = prod_{i=1}^{m-n} (m+n+i)/i; stored as (K, 0, 0, 0)
+__device__ double seed_norm(int m, int n) {
+  // sqrt(C(2m, m+n)), C(2m, m+n) = prod_{i=1}^{m-n} (m+n+i)/i
   double c = 1.0;
   for (int i = 1; i <= m - n; ++i) c = c * (m + n + i) / i;
-  K[4 * q] = sqrt(c);
-  K[4 * q + 1] = K[4 * q + 2] = K[4 * q + 3] = 0.0;
+  return sqrt(c);
+}
+
+// seedK[g] = (K(m, n_a), K(m, n_b), 0, 0) for partner group g; K of the empty
+// half is zero, so its recurrence stays at zero.
+__global__ void k_seedK(int ngroups, double *K) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  int m = 0;
+  while ((m + 1) * (m + 2) / 2 <= g) ++m;
+  int j = g - m * (m + 1) / 2, na = 2 * j - m;
+  K[4 * g] = seed_norm(m, na);
+  K[4 * g + 1] = na + 1 <= m ? seed_norm(m, na + 1) : 0.0;
+  K[4 * g + 2] = K[4 * g + 3] = 0.0;
 }
 
 __device__ double ipow_d(double x, int p) {
@@ -129,22 +140,23 @@ __device__ double ipow_d(double x, int p) {
 }
 
 // soft_d[k][pair_off0[q] + l - m] = d^l_mn(beta_k), l = m..L0, by the recurrence.
-__global__ void k_soft_d(int L0, int ns, int npairs0, const int *pair_off, const int *pair_off0,
+__global__ void k_soft_d(int L0, int ns, int npairs0, const int *pair_base, const int *pair_off0,
                          const double *rc, const double *K, long nc0, double *out) {
   int q = blockIdx.x, k = blockIdx.y;
   if (q >= npairs0 || threadIdx.x != 0) return;
   int m = 0;
   while ((m + 1) * (m + 1) <= q) ++m;
   int n = q - m * m - m;
+  int g = m * (m + 1) / 2 + ((n + m) >> 1), h = (n + m) & 1;
   double beta = M_PI * (2.0 * k + 1.0) / (2.0 * ns);
   double ch = cos(0.5 * beta), sh = sin(0.5 * beta), x = cos(beta);
-  double d = K[4 * q] * ipow_d(ch, m + n) * ipow_d(-sh, m - n), dp = 0.0;
+  double d = K[4 * g + h] * ipow_d(ch, m + n) * ipow_d(-sh, m - n), dp = 0.0;
   double *o = out + (long)k * nc0 + pair_off0[q];
-  const double *r = rc + 4L * pair_off[q];
+  const double *r = rc + pair_base[q];
   for (int l = m; l <= L0; ++l) {
     o[l - m] = d;
-    const double *c = r + 4 * (l - m);
-    double dn = (c[0] * x - c[1]) * d - c[2] * dp;
+    const double *c = r + 8 * (l - m);
+    double dn = (c[0] * x + c[2]) * d + c[4] * dp;
     dp = d; d = dn;
   }
 }
@@ -170,7 +182,7 @@ __global__ void k_to_float(const double *in, float *out, long n) {
 cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
-  size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.npairs;
+  size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.ngroups;
   size_t n_dcs = 2 * (size_t)(p.np / 2 - 1) * p.Mp;
   double *gx, *gw;
   cudaError_t e;
@@ -194,10 +206,10 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   k_ptab<<<(unsigned)((n_ptab + 127) / 128), 128, 0, st>>>(p.LJ, p.nt, p.np, p.xj, p.wj, ptab);
   k_twiddle<<<(p.np + 127) / 128, 128, 0, st>>>(p.np, phi);
   k_twiddle<<<(p.ns + 127) / 128, 128, 0, st>>>(p.ns, tw);
-  k_rcoef<<<p.npairs, 64, 0, st>>>(p.LJ, p.npairs, p.pair_off, rc);
-  k_seedK<<<(p.npairs + 127) / 128, 128, 0, st>>>(p.npairs, K);
+  k_rcoef<<<p.npairs, 64, 0, st>>>(p.LJ, p.npairs, p.pair_base, rc);
+  k_seedK<<<(p.ngroups + 127) / 128, 128, 0, st>>>(p.ngroups, K);
   k_dft_cs<<<(unsigned)((n_dcs / 2 + 127) / 128), 128, 0, st>>>(p.LJ, p.Mp, dcs);
-  k_soft_d<<<dim3(p.npairs0, p.ns), 32, 0, st>>>(p.L0, p.ns, p.npairs0, p.pair_off, p.pair_off0,
+  k_soft_d<<<dim3(p.npairs0, p.ns), 32, 0, st>>>(p.L0, p.ns, p.npairs0, p.pair_base, p.pair_off0,
                                                  rc, K, p.nc0, sd);
   if (!p.fp64) {
     struct { double *src; void *dst; size_t n; } cp[] = {

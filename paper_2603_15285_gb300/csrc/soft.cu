@@ -21,7 +21,7 @@ namespace matcha {
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_base,
             const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
             const T *__restrict__ tw, T *__restrict__ grid) {
   const int k = blockIdx.x;
@@ -34,14 +34,14 @@ k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restr
   const T *dk = soft_d + (long)k * nc0;
   for (int q = threadIdx.x; q < np0; q += blockDim.x) {
     int m = isqrt_floor(q), n = q - m * m - m;
-    const T *cp = cb + 4L * pair_off[q];
+    const T *cp = cb + pair_base[q];
     const T *dp = dk + pair_off0[q];
     T ar = 0, ai = 0, br = 0, bi = 0;
     for (int l = m; l <= L0; ++l) {
       T d = dp[l - m];
-      const T *e = cp + 4 * (l - m);
-      ar = fma(e[0], d, ar); ai = fma(e[1], d, ai);
-      br = fma(e[2], d, br); bi = fma(e[3], d, bi);
+      const T *e = cp + 8 * (l - m);
+      ar = fma(e[0], d, ar); ai = fma(e[2], d, ai);
+      br = fma(e[4], d, br); bi = fma(e[6], d, bi);
     }
     if ((m - n) & 1) { br = -br; bi = -bi; }  // d^l_nm = (-1)^{m-n} d^l_mn
     auto put = [&](int a, int bb, T re, T im) {
@@ -240,7 +240,7 @@ __device__ __forceinline__ bool is_local_max_smem(const float *g, int ns, int p)
 }
 
 __global__ void __launch_bounds__(FUSED_THREADS)
-k_soft_fused(const float *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+k_soft_fused(const float *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_base,
              const float *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
              const float *__restrict__ tw, int P_max, const int *__restrict__ P_per,
              float *__restrict__ grid_out, int *__restrict__ idx_out,
@@ -259,14 +259,14 @@ k_soft_fused(const float *__restrict__ c, long nc, int L0, int ns, const int *__
       int kk = t / np0, q = t - kk * np0, k = k0 + kk;
       if (k >= ns) continue;
       int m = isqrt_floor(q), n = q - m * m - m;
-      const float *cp = cb + 4L * pair_off[q];
+      const float *cp = cb + pair_base[q];
       const float *dp = soft_d + (long)k * nc0 + pair_off0[q];
       float ar = 0, ai = 0, br = 0, bi = 0;
       for (int l = m; l <= L0; ++l) {
         float d = dp[l - m];
-        const float *e = cp + 4 * (l - m);
-        ar = fmaf(e[0], d, ar); ai = fmaf(e[1], d, ai);
-        br = fmaf(e[2], d, br); bi = fmaf(e[3], d, bi);
+        const float *e = cp + 8 * (l - m);
+        ar = fmaf(e[0], d, ar); ai = fmaf(e[2], d, ai);
+        br = fmaf(e[4], d, br); bi = fmaf(e[6], d, bi);
       }
       if ((m - n) & 1) { br = -br; bi = -bi; }
       float *S = Sg + 2 * kk * W * W;
@@ -421,7 +421,7 @@ constexpr int STREAM_THREADS = 256;
 
 template <typename T>
 __device__ void stream_slice(const T *cb, int L0, int ns, int k,
-                             const int *__restrict__ pair_off, const T *__restrict__ soft_d,
+                             const int *__restrict__ pair_base, const T *__restrict__ soft_d,
                              const int *__restrict__ pair_off0, long nc0, const T *__restrict__ tw,
                              T *Sg, T *G, T *dst) {
   const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1), tid = threadIdx.x, NT = blockDim.x;
@@ -481,7 +481,7 @@ __device__ void stream_slice(const T *cb, int L0, int ns, int k,
 
 template <typename T>
 __global__ void __launch_bounds__(STREAM_THREADS)
-k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_base,
               const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
               const T *__restrict__ tw, int P_max, const int *__restrict__ P_per,
               T *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
@@ -508,9 +508,9 @@ k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__res
       int q = dl.div(t), e = t - q * (L0 + 1);
       int m = isqrt_floor(q);
       if (e <= L0 - m) {
-        const T *src = cg + 4L * (pair_off[q] + e);
+        const T *src = cg + pair_base[q] + 8L * e;
         T *dst = cst + 4L * (pair_off0[q] + e);
-        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+        dst[0] = src[0]; dst[1] = src[2]; dst[2] = src[4]; dst[3] = src[6];
       }
     }
   }
@@ -520,11 +520,11 @@ k_soft_stream(const T *__restrict__ c, long nc, int L0, int ns, const int *__res
   if (tid < 32) { rv[tid] = 0; ri[tid] = INT_MAX; }
   if (tid == 0) counters[1] = 0;
   __syncthreads();
-  stream_slice(cb, L0, ns, 0, pair_off, soft_d, pair_off0, nc0, tw, Sg, G, ring);
-  if (ns > 1) stream_slice(cb, L0, ns, 1, pair_off, soft_d, pair_off0, nc0, tw, Sg, G, ring + n2);
+  stream_slice(cb, L0, ns, 0, pair_base, soft_d, pair_off0, nc0, tw, Sg, G, ring);
+  if (ns > 1) stream_slice(cb, L0, ns, 1, pair_base, soft_d, pair_off0, nc0, tw, Sg, G, ring + n2);
   for (int k = 0; k < ns; ++k) {
     if (k >= 1 && k + 1 < ns)
-      stream_slice(cb, L0, ns, k + 1, pair_off, soft_d, pair_off0, nc0, tw, Sg, G,
+      stream_slice(cb, L0, ns, k + 1, pair_base, soft_d, pair_off0, nc0, tw, Sg, G,
                    ring + ((k + 1) % 3) * n2);
     const T *cur = ring + (k % 3) * n2;
     const T *sls[3] = {ring + ((k + 2) % 3) * n2, cur, ring + ((k + 1) % 3) * n2};
@@ -624,7 +624,7 @@ __device__ __forceinline__ typename Vec4<T>::type ld4(const T *p) {
 
 template <typename T, int KB>
 __global__ void __launch_bounds__(CHUNK_THREADS, sizeof(T) == 8 ? 1 : 2)
-k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_off,
+k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_base,
              const T *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
              const T *__restrict__ tw, int P_max, const int *__restrict__ P_per,
              T *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
@@ -678,9 +678,9 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
       int q = dl.div(t), e = t - q * (L0 + 1);
       int m = isqrt_floor(q);
       if (e <= L0 - m) {
-        const T *src = cg + 4L * (pair_off[q] + e);
+        const T *src = cg + pair_base[q] + 8L * e;
         T *dst = cst + 4L * (pair_off0[q] + e);
-        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+        dst[0] = src[0]; dst[1] = src[2]; dst[2] = src[4]; dst[3] = src[6];
       }
     }
   }
@@ -878,7 +878,7 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
       cudaFuncSetAttribute(k_soft_chunk<T, SOFT_KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       k_soft_chunk<T, SOFT_KB><<<B, CHUNK_THREADS, smem, st>>>(
-          c, p.nc, p.L0, p.ns, p.pair_off, (const T *)p.soft_d, p.pair_off0, p.nc0,
+          c, p.nc, p.L0, p.ns, p.pair_base, (const T *)p.soft_d, p.pair_off0, p.nc0,
           (const T *)p.soft_tw, p.P, P_per, grid, idx, euler, score, n_cand);
       return cudaGetLastError();
     }
@@ -888,7 +888,7 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
     if (smem <= 227 * 1024 - 1024) {
       cudaFuncSetAttribute(k_soft_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_soft_stream<T><<<B, STREAM_THREADS, smem, st>>>(
-          c, p.nc, p.L0, p.ns, p.pair_off, (const T *)p.soft_d, p.pair_off0, p.nc0,
+          c, p.nc, p.L0, p.ns, p.pair_base, (const T *)p.soft_d, p.pair_off0, p.nc0,
           (const T *)p.soft_tw, p.P, P_per, grid, idx, euler, score, n_cand);
       return cudaGetLastError();
     }
@@ -897,13 +897,13 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
     size_t smem = soft_fused_smem(p);
     cudaFuncSetAttribute(k_soft_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_soft_fused<<<B, FUSED_THREADS, smem, st>>>(
-        (const float *)c, p.nc, p.L0, p.ns, p.pair_off, (const float *)p.soft_d, p.pair_off0,
+        (const float *)c, p.nc, p.L0, p.ns, p.pair_base, (const float *)p.soft_d, p.pair_off0,
         p.nc0, (const float *)p.soft_tw, p.P, P_per, (float *)grid, idx, euler, score, n_cand);
     return cudaGetLastError();
   }
   int W = 2 * p.L0 + 1;
   size_t smem = sizeof(T) * (2 * (size_t)W * W + 2 * (size_t)(p.L0 + 1) * p.ns);
-  k_soft_grid<T><<<dim3(p.ns, B), 256, smem, st>>>(c, p.nc, p.L0, p.ns, p.pair_off,
+  k_soft_grid<T><<<dim3(p.ns, B), 256, smem, st>>>(c, p.nc, p.L0, p.ns, p.pair_base,
                                                    (const T *)p.soft_d, p.pair_off0, p.nc0,
                                                    (const T *)p.soft_tw, grid);
   k_topk<T><<<B, TOPK_THREADS, 0, st>>>(grid, p.ns, p.P, P_per, idx, euler, score, n_cand);

@@ -11,11 +11,14 @@ def coef_to_complex(t):
 
 
 def corr_to_oracle(c_gpu_one, L):
-    """Library pair layout [nc][2][2] -> the oracle's full c^l_mn array."""
-    a = c_gpu_one.detach().cpu().double().numpy()
+    """Library grouped layout [nc][2][2] -> the oracle's full c^l_mn array."""
+    a = m.corr_pairs(c_gpu_one.detach().cpu().double().numpy())
     z = a[..., 0] + 1j * a[..., 1]          # [nc][2]
     out = np.zeros(O.c_size(L), complex)
     for e, (mm, nn, l) in enumerate(m.corr_layout(L)):
+        if nn > mm:                          # empty partner slot
+            assert z[e, 0] == 0 and z[e, 1] == 0
+            continue
         out[O.c_index(l, mm, nn)] = z[e, 0]
         out[O.c_index(l, nn, mm)] = z[e, 1]
     # negative images: c_{-m,-n} = (-1)^{m+n} conj(c_mn)

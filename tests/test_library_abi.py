@@ -5,7 +5,9 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
+import torch
 
 import paper_2603_15285_gb300 as m
 from paper_2603_15285_gb300 import build as libbuild
@@ -80,5 +82,22 @@ def test_null_handles_are_rejected(L):
 def test_layout_helper_counts_entries():
     for Lj in (8, 16, 32):
         rows = m.corr_layout(Lj)
-        assert len(rows) == sum((l + 1) ** 2 for l in range(Lj + 1))
-        assert len(rows) == sum((2 * mm + 1) * (Lj - mm + 1) for mm in range(Lj + 1))
+        used = rows[rows[:, 1] <= rows[:, 0]]
+        # every (l, m, n) with m >= |n| once, plus one empty slot per (m, l)
+        assert len(used) == sum((l + 1) ** 2 for l in range(Lj + 1))
+        assert len(set(map(tuple, used))) == len(used)
+        assert len(rows) - len(used) == sum(Lj - mm + 1 for mm in range(Lj + 1))
+        assert len(rows) == 2 * sum((mm + 1) * (Lj - mm + 1) for mm in range(Lj + 1))
+
+
+def test_corr_pairs_deinterleaves_partners():
+    # group entry e holds reals 8e + 2k + h: component k of slot h
+    n = 6
+    raw = np.arange(4 * n, dtype=np.float64).reshape(n, 2, 2)
+    rows = m.corr_pairs(raw)
+    for e in range(n // 2):
+        for h in range(2):
+            got = rows[2 * e + h].reshape(4)
+            assert list(got) == [8 * e + 2 * k + h for k in range(4)]
+    t = torch.arange(4 * n, dtype=torch.float64).reshape(1, n, 2, 2)
+    assert np.array_equal(m.corr_pairs(t)[0].numpy(), rows)
