@@ -30,14 +30,19 @@
  *   SH coefficients (matcha_analyze):  [b][s][lm] complex, lm = l(l+1)/2 + m,
  *     0 <= m <= l <= L_J, s < n_shells.  Negative orders of these real volumes
  *     follow from f_{l,-m} = (-1)^m conj(f_{lm}).
- *   correlation coefficients (matcha_correlate_coeffs): per particle,
- *     for each order pair (m, n) with 0 <= m <= L_J and -m <= n <= m (pair
- *     index q = m*m + n + m, pairs in increasing q), for l = m .. L_J, the two
- *     complex numbers (c^l_{mn}, c^l_{nm}).  Entry (q, l) starts at complex
- *     index 2 * (off(m, n) + l - m) with
- *     off(m, n) = sum_{m' < m} (2m'+1)(L_J-m'+1) + (n+m)(L_J-m+1);
- *     matcha_plan_info() returns the entry count.  These pairs and their
- *     images under c^l_{-m,-n} = (-1)^{m+n} conj(c^l_{mn}) give every
+ *   correlation coefficients (matcha_correlate_coeffs): per particle, the
+ *     order pairs (m, n) with 0 <= m <= L_J and -m <= n <= m, taken two at a
+ *     time with equal m: group g = m(m+1)/2 + j (j = 0..m) holds the
+ *     partners n_a = 2j - m (slot 0) and n_b = n_a + 1 (slot 1; for j = m
+ *     slot 1 is empty and holds zeros).  Group g covers l = m .. L_J; entry
+ *     (g, l) is 8 reals starting at real 8 * (goff(m, j) + l - m) with
+ *     goff(m, j) = sum_{m' < m} (m'+1)(L_J-m'+1) + j (L_J-m+1), and real
+ *     2k + h of it is component k of slot h, k = 0..3 being Re c^l_{mn},
+ *     Im c^l_{mn}, Re c^l_{nm}, Im c^l_{nm}.  The partners' equal components
+ *     sit side by side so that both advance in one paired operation.
+ *     matcha_plan_info() returns corr_entries = 2 * (number of (g, l)
+ *     entries), so a particle holds corr_entries * 4 reals.  These pairs and
+ *     their images under c^l_{-m,-n} = (-1)^{m+n} conj(c^l_{mn}) give every
  *     coefficient with |m|, |n| <= l <= L_J.
  *   SOFFT grid (workspace): n = 2K(L0+1) points per angle, alpha_i = 2 pi i/n,
  *     beta_k = pi (2k+1)/(2n), gamma_j = 2 pi j/n, linear index (i n + k) n + j.
@@ -107,7 +112,7 @@ typedef struct {
 typedef struct {
   int n_lm;            /* (L_J+1)(L_J+2)/2 SH coefficients per shell */
   long coeff_count;    /* complex SH coefficients per volume = n_shells * n_lm */
-  long corr_entries;   /* (pair, l) entries per particle; 2 complex each */
+  long corr_entries;   /* (pair slot, l) entries per particle, empty slots included; 2 complex each */
   int n_pairs;         /* (L_J+1)^2 order pairs */
   int soft_n;          /* SOFFT points per angle, 2K(L0+1) */
   int real_bytes;      /* 8 (FP64) or 4 (FP32) */

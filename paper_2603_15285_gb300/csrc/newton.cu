@@ -63,7 +63,8 @@ template <> __device__ __forceinline__ double tcos<double>(double x) { return co
 template <> __device__ __forceinline__ double tsin<double>(double x) { return sin(x); }
 
 struct SmemLayout {
-  double *th, *tr, *del, *Cc, *res, *red;
+  double *th, *tr, *del, *Cc, *res;
+  void *red;  // [warps][P][10] working precision
   int *state, *steps, *tries, *fl;
   void *evp, *ea, *pw, *stage;
 };
@@ -159,13 +160,16 @@ __device__ __forceinline__ Group group_of(int g, int LJ) {
 // -b_b, -e_a, -e_b, 0, 0); L_J + 1 entries.
 __host__ __device__ __forceinline__ int stage_half(int LJ) { return 4 + 16 * (LJ + 1); }
 
-// Power tables: per candidate two rows (cos(b/2)^k, sin(b/2)^k) of PW_PAD
-// zeros followed by k = 0 .. 2 L_J + 3.
+// Per-candidate tables, candidate index fastest with an odd stride
+// cand_stride(P) >= P, so the lanes of a sub-slot (one candidate each) read
+// distinct banks.  Power table: two rows (cos(b/2)^k, sin(b/2)^k), each
+// PW_PAD zeros followed by k = 0 .. 2 L_J + 3.  Phase table: four rows
+// (cos k a, sin k a, cos k g, sin k g) for k = -L_J .. L_J + 1 (index k + L_J).
+// Element (row r, position k, candidate p) is at (r * row_len + k) * stride + p.
 constexpr int PW_PAD = 4;
 __host__ __device__ __forceinline__ int pw_row(int LJ) { return PW_PAD + 2 * LJ + 4; }
-// Phase tables: per candidate four rows (cos k a, sin k a, cos k g, sin k g)
-// for k = -L_J .. L_J + 1 (index k + L_J).
 __host__ __device__ __forceinline__ int ph_row(int LJ) { return 2 * LJ + 2; }
+__host__ __device__ __forceinline__ int cand_stride(int P) { return P | 1; }
 
 // Seeds at l = m of both halves: d = sigma K ch^a sh^b with a = m+n,
 // b = m-n, sigma = (-1)^b; with FULL also d' and d'' (Appendix A.4 applied to
@@ -173,11 +177,11 @@ __host__ __device__ __forceinline__ int ph_row(int LJ) { return 2 * LJ + 2; }
 // The first half has a = aa, b = ba (both even, so sigma = +1); the second
 // a = aa + 1, b = ba - 1 (sigma = -1).  pc, ps: shared addresses of ch^aa,
 // sh^ba in the padded power tables; a term whose integer coefficient is zero
-// may read a zero pad, so it adds exactly 0.
+// may read a zero pad, so it adds exactly 0.  z: bytes between consecutive
+// powers in the table.
 template <typename T, bool FULL>
-__device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, v2<T> K, int aa, int ba,
-                                           v2<T> &D0, v2<T> &D1, v2<T> &D2) {
-  constexpr unsigned z = sizeof(T);
+__device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, unsigned z, v2<T> K, int aa,
+                                           int ba, v2<T> &D0, v2<T> &D1, v2<T> &D2) {
   T c0, c1, s0, sm1;
   lds1(pc, c0); lds1(pc + z, c1);
   lds1(ps, s0); lds1(ps - z, sm1);
@@ -348,10 +352,10 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
                                          const double *pts, const int *need, SmemLayout &sm) {
   constexpr unsigned z = sizeof(T);
   const int P = A.P, cpw = A.cpw, LJ = A.LJ;
-  const int NPW = pw_row(LJ), RW = ph_row(LJ);
+  const int NPW = pw_row(LJ), RW = ph_row(LJ), PS = cand_stride(P);
   T *evp = (T *)sm.evp;  // [P][8]: x, s, ch, sh, cos a, sin a, cos g, sin g
-  T *ph = (T *)sm.ea;    // [P][4][RW]: cos k a, sin k a, cos k g, sin k g
-  T *pw = (T *)sm.pw;    // [P][2][NPW]: PW_PAD zeros, then ch^k (sh^k), k = 0..2LJ+3
+  T *ph = (T *)sm.ea;    // [4][RW][PS]: cos k a, sin k a, cos k g, sin k g
+  T *pw = (T *)sm.pw;    // [2][NPW][PS]: PW_PAD zeros, then ch^k (sh^k), k = 0..2LJ+3
   const int tid = threadIdx.x;
   if (tid < P && need[tid]) {
     T al = (T)pts[3 * tid], be = (T)pts[3 * tid + 1], ga = (T)pts[3 * tid + 2];
@@ -367,20 +371,20 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   for (int t = tid; t < 2 * P * npk; t += blockDim.x) {
     int pr = dw.div(t), k = t - pr * npk;
     int p = pr >> 1, which = pr & 1;
-    if (need[p]) pw[pr * NPW + PW_PAD + k] = ipow_t(evp[8 * p + 2 + which], k);
+    if (need[p]) pw[(which * NPW + PW_PAD + k) * PS + p] = ipow_t(evp[8 * p + 2 + which], k);
   }
   if (tid < 2 * P) {
     int p = tid >> 1, which = tid & 1;
     if (need[p]) {
       T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
-      T *cr_ = ph + ((long)p * 4 + 2 * which) * RW + LJ, *ci_ = cr_ + RW;
+      T *cr_ = ph + ((2 * which) * RW + LJ) * PS + p, *ci_ = cr_ + RW * PS;
       T cr = 1, ci = 0;
       cr_[0] = 1; ci_[0] = 0;
       for (int m = 1; m <= L + 1; ++m) {
         T nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
         cr = nr; ci = ni;
-        cr_[m] = cr; ci_[m] = ci;
-        if (m <= L) { cr_[-m] = cr; ci_[-m] = -ci; }
+        cr_[m * PS] = cr; ci_[m * PS] = ci;
+        if (m <= L) { cr_[-m * PS] = cr; ci_[-m * PS] = -ci; }
       }
     }
   }
@@ -398,10 +402,11 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   const T xb = evp[8 * pc], sb = evp[8 * pc + 1];
   const v2<T> X = vset<T>(xb, xb), NS = vset<T>(-sb, -sb), NX = vset<T>(-xb, -xb);
   // shared addresses of this candidate's tables (index 0 of each row)
-  const unsigned pcu = smem_u32(pw + (2 * pc) * NPW + PW_PAD);
-  const unsigned psu = pcu + z * NPW;
-  const unsigned eacu = smem_u32(ph + (long)pc * 4 * RW + LJ);  // k = 0 of cos k a
-  const unsigned easu = eacu + z * RW, egcu = easu + z * RW, egsu = egcu + z * RW;
+  const unsigned zs = z * PS;  // bytes between consecutive positions of a row
+  const unsigned pcu = smem_u32(pw + PW_PAD * PS + pc);
+  const unsigned psu = pcu + zs * NPW;
+  const unsigned eacu = smem_u32(ph + LJ * PS + pc);  // k = 0 of cos k a
+  const unsigned easu = eacu + zs * RW, egcu = easu + zs * RW, egsu = egcu + zs * RW;
   v2<T> acc[10];
 #pragma unroll
   for (int i = 0; i < 10; ++i) acc[i] = vset<T>(T(0), T(0));
@@ -424,27 +429,36 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
       cp_async16s(dst, src);
     if (p < 4 / CH) cp_async16s(hb + 16 * p, seedK + 4L * g + CH * p);
   };
+  // Sub-slot `slot` takes group k * nslots + slot in even rounds k and
+  // k * nslots + (nslots - 1 - slot) in odd ones: groups come in increasing g
+  // (non-increasing length), so the alternating order balances the sub-slots
+  // while keeping every sum's order fixed.
+  auto group_at = [&](int k) {
+    return k * nslots + ((k & 1) ? nslots - 1 - slot : slot);
+  };
   if (slot < nslots && slot < ng) {
-    int cur = 0;
-    Group nx = group_of(slot, LJ);
-    issue(nx, slot, stg);
+    int cur = 0, k = 0;
+    int g = group_at(0);
+    Group gc = group_of(g, LJ);
+    issue(gc, g, stg);
     cp_async_commit();
-    for (int g = slot; g < ng; g += nslots) {
-      const Group G = nx;
-      if (g + nslots < ng) {
-        nx = group_of(g + nslots, LJ);
-        issue(nx, g + nslots, stg + (cur ^ 1) * HB);
+    while (g < ng) {
+      const int gn = group_at(k + 1);
+      Group gnx = gc;
+      if (gn < ng) {
+        gnx = group_of(gn, LJ);
+        issue(gnx, gn, stg + (cur ^ 1) * HB);
       }
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp(submask);
       if (act) {
-        const int m = G.m, na = G.na, aa = m + na, ba = m - na;
+        const int m = gc.m, na = gc.na, aa = m + na, ba = m - na;
         const unsigned buf = stg + cur * HB;
         v2<T> K, D0, D1, D2, Z[12];
         lds2(buf, K);
         D1 = D2 = vset<T>(T(0), T(0));
-        group_seed<T, FULL>(pcu + z * aa, psu + z * ba, K, aa, ba, D0, D1, D2);
+        group_seed<T, FULL>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
         group_sum<T, FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
         const T fm = T(m), fa = T(na);
         const v2<T> MM = vset<T>(fm, fm), NN = vset<T>(fa, fa + T(1));
@@ -453,10 +467,10 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
         {
           v2<T> ER, EI, NEI;
           T ar, ai;
-          lds1(eacu + z * m, ar);
-          lds1(easu + z * m, ai);
-          phase<T>(vset<T>(ar, ar), vset<T>(ai, ai), vld<T>(egcu + z * na, egcu + z * (na + 1)),
-                   vld<T>(egsu + z * na, egsu + z * (na + 1)), ER, EI, NEI);
+          lds1(eacu + zs * m, ar);
+          lds1(easu + zs * m, ai);
+          phase<T>(vset<T>(ar, ar), vset<T>(ai, ai), vld<T>(egcu + zs * na, egcu + zs * (na + 1)),
+                   vld<T>(egsu + zs * na, egsu + zs * (na + 1)), ER, EI, NEI);
           const v2<T> Wt = vset<T>(m == 0 ? T(1) : T(2), na < m ? T(2) : T(0));
           add_image<T, FULL>(acc, Wt, MM, NN, ER, EI, NEI, Z[0], Z[1], Z[4], Z[5], Z[8], Z[9]);
         }
@@ -465,10 +479,10 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
         {
           v2<T> ER, EI, NEI;
           T gr, gi;
-          lds1(egcu + z * m, gr);
-          lds1(egsu + z * m, gi);
-          phase<T>(vld<T>(eacu + z * na, eacu + z * (na + 1)),
-                   vld<T>(easu + z * na, easu + z * (na + 1)), vset<T>(gr, gr), vset<T>(gi, gi),
+          lds1(egcu + zs * m, gr);
+          lds1(egsu + zs * m, gi);
+          phase<T>(vld<T>(eacu + zs * na, eacu + zs * (na + 1)),
+                   vld<T>(easu + zs * na, easu + zs * (na + 1)), vset<T>(gr, gr), vset<T>(gi, gi),
                    ER, EI, NEI);
           const v2<T> Wt = vset<T>(na == m || na == -m ? T(0) : T(2), na + 1 < m ? T(-2) : T(0));
           add_image<T, FULL>(acc, Wt, NN, MM, ER, EI, NEI, Z[2], Z[3], Z[6], Z[7], Z[10], Z[11]);
@@ -476,6 +490,9 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
       }
       __syncwarp(submask);
       cur ^= 1;
+      ++k;
+      g = gn;
+      gc = gnx;
     }
     cp_async_wait<0>();
   }
@@ -492,25 +509,29 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   if (lane < cpw && p < P)
 #pragma unroll
     for (int i = 0; i < 10; ++i)
-      if (i < nq) sm.red[(warp * P + p) * 10 + i] = (double)r[i];
+      if (i < nq) ((T *)sm.red)[(warp * P + p) * 10 + i] = r[i];
   __syncthreads();
   for (int idx = tid; idx < P * nq; idx += blockDim.x) {
     int pp = idx / nq, i = idx - pp * nq;
     if (need[pp]) {
-      double v = 0;
-      for (int w = 0; w < NEWTON_WARPS; ++w) v += sm.red[(w * P + pp) * 10 + i];
-      sm.res[pp * 10 + i] = v;
+      T v = 0;
+      for (int w = 0; w < NEWTON_WARPS; ++w) v += ((const T *)sm.red)[(w * P + pp) * 10 + i];
+      sm.res[pp * 10 + i] = (double)v;
     }
   }
   __syncthreads();
 }
 
+// x mod 2 pi in [0, 2 pi).  The refinement only meets |x| < 4 pi (a wrapped
+// angle plus a clamped step, or plus pi after a reflection of beta), where a
+// few compare-and-add steps give the same result as x - 2 pi floor(x / 2 pi)
+// without a double-precision division; other inputs take that formula first.
 __device__ __forceinline__ double mod2pi_d(double x) {
   const double t = 2.0 * M_PI;
-  double r = x - t * floor(x / t);
-  if (r >= t) r -= t;
-  if (r < 0) r += t;
-  return r;
+  if (!(x < 4.0 * t && x >= -4.0 * t)) x -= t * floor(x / t);
+  for (int k = 0; k < 4 && x >= t; ++k) x -= t;
+  for (int k = 0; k < 4 && x < 0.0; ++k) x += t;
+  return x;
 }
 
 __device__ __forceinline__ void wrap_d(double *v) {
@@ -520,73 +541,88 @@ __device__ __forceinline__ void wrap_d(double *v) {
   v[0] = mod2pi_d(a); v[1] = b; v[2] = mod2pi_d(g);
 }
 
-// Newton direction from grad g and Hessian H (row-major 3x3); returns flag bits.
-__device__ __forceinline__ int newton_dir(const double *g, const double *H, int L, double *d) {
-  double hn = 0;
+// Newton direction from grad g and Hessian H (row-major 3x3) in the working
+// precision S; returns flag bits.  A Cholesky pivot of -H counts as positive
+// above piv_rel ||H||_F (1e-12 in FP64, 1e-6 in FP32: above the rounding
+// level of H's entries).
+template <typename S>
+__device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d) {
+  const S piv_rel = sizeof(S) == 8 ? S(1e-12) : S(1e-6);
+  S hn = 0;
+#pragma unroll
   for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
   hn = sqrt(hn);
-  const double tol = 1e-12 * hn;
+  const S tol = piv_rel * hn;
   // Cholesky of A = -H
-  double a00 = -H[0], a10 = -H[3], a20 = -H[6], a11 = -H[4], a21 = -H[7], a22 = -H[8];
+  S a00 = -H[0], a10 = -H[3], a20 = -H[6], a11 = -H[4], a21 = -H[7], a22 = -H[8];
   bool ok = a00 > tol;
-  double L00 = 0, L10 = 0, L20 = 0, L11 = 0, L21 = 0, L22 = 0;
+  S L00 = 0, L10 = 0, L20 = 0, L11 = 0, L21 = 0, L22 = 0;
   if (ok) {
     L00 = sqrt(a00); L10 = a10 / L00; L20 = a20 / L00;
-    double p11 = a11 - L10 * L10;
+    S p11 = a11 - L10 * L10;
     ok = p11 > tol;
     if (ok) {
       L11 = sqrt(p11); L21 = (a21 - L20 * L10) / L11;
-      double p22 = a22 - L20 * L20 - L21 * L21;
+      S p22 = a22 - L20 * L20 - L21 * L21;
       ok = p22 > tol;
       if (ok) L22 = sqrt(p22);
     }
   }
   int fl = 0;
   if (ok) {
-    double y0 = g[0] / L00;
-    double y1 = (g[1] - L10 * y0) / L11;
-    double y2 = (g[2] - L20 * y0 - L21 * y1) / L22;
-    double x2 = y2 / L22;
-    double x1 = (y1 - L21 * x2) / L11;
-    double x0 = (y0 - L10 * x1 - L20 * x2) / L00;
+    S y0 = g[0] / L00;
+    S y1 = (g[1] - L10 * y0) / L11;
+    S y2 = (g[2] - L20 * y0 - L21 * y1) / L22;
+    S x2 = y2 / L22;
+    S x1 = (y1 - L21 * x2) / L11;
+    S x0 = (y0 - L10 * x1 - L20 * x2) / L00;
     d[0] = x0; d[1] = x1; d[2] = x2;
   } else {
     fl = 2;
-    for (int i = 0; i < 3; ++i) d[i] = hn > 0 ? g[i] / hn : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = hn > 0 ? g[i] / hn : S(0);
   }
-  double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  double cap = M_PI / (2.0 * (L + 1.0));
-  if (nrm > cap)
-    for (int i = 0; i < 3; ++i) d[i] *= cap / nrm;
+  S nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  S cap = S(M_PI / (2.0 * (L + 1.0)));
+  if (nrm > cap) {
+    S f = cap / nrm;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] *= f;
+  }
   return fl;
 }
 
 // Candidate tid has C, grad, H of its current point in res: record C, stop on
-// a non-finite value (flag bit 0), take the Newton direction, stop the level
-// when the increment is below step_tol, else prepare the first trial.
+// a non-finite value (flag bit 0), take the Newton direction (in the working
+// precision S), stop the level when the increment is below step_tol, else
+// prepare the first trial (angles in FP64).
+template <typename S>
 __device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) {
   const double *r = sm.res + 10 * tid;
-  double C = r[0], g[3] = {r[1], r[2], r[3]};
-  double H[9] = {r[4], r[5], r[6], r[5], r[7], r[8], r[6], r[8], r[9]};
-  bool fin = isfinite(C);
-  for (int i = 0; i < 3; ++i) fin = fin && isfinite(g[i]);
-  for (int i = 0; i < 9; ++i) fin = fin && isfinite(H[i]);
+  const double C = r[0];
+  const S g[3] = {S(r[1]), S(r[2]), S(r[3])};
+  const S H[9] = {S(r[4]), S(r[5]), S(r[6]), S(r[5]), S(r[7]), S(r[8]), S(r[6]), S(r[8]), S(r[9])};
+  bool fin = true;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) fin = fin && isfinite(r[i]);
   sm.Cc[tid] = C;
   if (!fin) {
     sm.fl[tid] |= 1;
     sm.state[tid] = ST_DEAD;
     return;
   }
-  double d[3];
-  sm.fl[tid] |= newton_dir(g, H, L, d);
-  if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < A.tol) {
+  S d[3];
+  sm.fl[tid] |= newton_dir<S>(g, H, L, d);
+  if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < S(A.tol)) {
     sm.state[tid] = ST_STOP;
     return;
   }
-  double tr[3] = {sm.th[3 * tid] + d[0], sm.th[3 * tid + 1] + d[1], sm.th[3 * tid + 2] + d[2]};
+  double tr[3] = {sm.th[3 * tid] + (double)d[0], sm.th[3 * tid + 1] + (double)d[1],
+                  sm.th[3 * tid + 2] + (double)d[2]};
   wrap_d(tr);
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
-    sm.del[3 * tid + i] = d[i];
+    sm.del[3 * tid + i] = (double)d[i];
     sm.tr[3 * tid + i] = tr[i];
   }
   sm.tries[tid] = 0;
@@ -609,7 +645,6 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
   sm.del = dp; dp += 3 * P;
   sm.Cc = dp; dp += P;
   sm.res = dp; dp += 10 * P;
-  sm.red = dp; dp += 10 * P * NEWTON_WARPS;
   int *ip = reinterpret_cast<int *>(dp);
   sm.state = ip; ip += P;
   sm.steps = ip; ip += P;
@@ -619,14 +654,16 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
   uintptr_t u = reinterpret_cast<uintptr_t>(ip);
   u = (u + 15) & ~uintptr_t(15);
   T *tp = reinterpret_cast<T *>(u);
+  sm.red = tp; tp += 10 * P * NEWTON_WARPS;
   sm.evp = tp; tp += 8 * P;
-  sm.ea = tp; tp += 4 * P * ph_row(A.LJ);  // phase rows
-  sm.pw = tp; tp += 2 * P * pw_row(A.LJ);
+  sm.ea = tp; tp += 4 * cand_stride(P) * ph_row(A.LJ);  // phase rows
+  sm.pw = tp; tp += 2 * cand_stride(P) * pw_row(A.LJ);
   tp = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(tp) + 31) & ~uintptr_t(31));
-  sm.stage = tp;  // [slots][2][L_J+1][8]
+  sm.stage = tp;  // [slots][2][stage_half(L_J)]
 
   const int nc_b = n_cand[b];
-  for (int t = tid; t < 2 * P * pw_row(A.LJ); t += blockDim.x) ((T *)sm.pw)[t] = T(0);  // pads
+  for (int t = tid; t < 2 * cand_stride(P) * pw_row(A.LJ); t += blockDim.x)
+    ((T *)sm.pw)[t] = T(0);  // pads
   if (tid < P) {
     double *e = euler + 3 * (b * P + tid);
     sm.th[3 * tid] = e[0]; sm.th[3 * tid + 1] = e[1]; sm.th[3 * tid + 2] = e[2];
@@ -656,7 +693,7 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
     evaluate<T, true>(A, L, cb, rcoef, seedK, sm.th, need, sm);
     if (tid < P && need[tid]) {
       sm.steps[tid] = 0;
-      start_step(tid, L, A, sm);
+      start_step<T>(tid, L, A, sm);
     }
     for (int round = 0; round < 3 * A.M; ++round) {
       int tw = 0, wf = 0;
@@ -678,7 +715,7 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
           sm.Cc[tid] = Ct;
           if (sm.steps[tid] < A.M - 1) {
             ++sm.steps[tid];
-            start_step(tid, L, A, sm);  // derivatives at the accepted point
+            start_step<T>(tid, L, A, sm);  // derivatives at the accepted point
           } else {
             sm.state[tid] = ST_STOP;
           }
@@ -720,10 +757,11 @@ static int newton_cpw(int P) { return P <= 16 ? 16 : 32; }
 // Shared memory of k_newton with `slots` staging buffers.
 static size_t newton_smem_bytes(const Plan &p, size_t tsize, int slots) {
   size_t P = p.P;
-  size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P + 10 * P * NEWTON_WARPS);
+  size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
-  bytes += tsize * (8 * P + 4 * P * ph_row(p.LJ) + 2 * P * pw_row(p.LJ)) + 32;
+  const size_t PS = cand_stride(p.P);
+  bytes += tsize * (10 * P * NEWTON_WARPS + 8 * P + 4 * PS * ph_row(p.LJ) + 2 * PS * pw_row(p.LJ)) + 32;
   bytes += tsize * (size_t)slots * 2 * stage_half(p.LJ);
   return bytes;
 }
