@@ -132,7 +132,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(256)
 k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const double *__restrict__ rs, const double *__restrict__ xj, const T *__restrict__ phi_cs,
-           const T *__restrict__ dcs, int Mp, const T *__restrict__ ptabT,
+           const T *__restrict__ dcs, int Mp, int Qf, int Mq, const T *__restrict__ ptabT,
            T *__restrict__ out) {
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
@@ -146,15 +146,15 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   T *SM = SP + K1 * Rp;                     // [K1][Rp]
   T *E0 = SM + K1 * Rp;                     // [Rp]  f_0
   T *EH = E0 + Rp;                          // [Rp]  f_{np/2}
-  T *CS = EH + Rp;                          // [2][K1][Mp]
-  T *F = CS + 2 * K1 * Mp;                  // [Rp][Mp] complex
+  T *CS = EH + Rp;                          // [2][2][Qf][Mq] folded DFT table
+  T *F = CS + 4 * Qf * Mq;                  // [Rp][Mp] complex
   T *RH = F + 2 * Rp * Mp;                  // [Rp] ring radius r_s sin(t_j)
   T *RZ = RH + Rp;                          // [Rp] ring height c0 + r_s cos(t_j)
   T *PH = RZ + Rp;                          // [np][2] cos, sin phi_k
   const float *vol = vols + b * N * N * N;
   const long NN = (long)N * N;
 
-  for (int t = tid; t < 2 * K1 * Mp; t += NT) CS[t] = dcs[t];
+  for (int t = tid; t < 4 * Qf * Mq; t += NT) CS[t] = dcs[t];
   // zero the padding rings
   for (int t = R + tid; t < Rp; t += NT) {
     E0[t] = 0; EH[t] = 0;
@@ -232,55 +232,86 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     }
   }
   __syncthreads();
-  // 2. folded DFT, 4 x 4 tiles of (ring, order)
-  const int tr = Rp / 4, tm = Mp / 4;
-  const FastDiv dtm(tm);
-  for (int t = tid; t < tr * tm; t += NT) {
-    int tq = dtm.div(t);
-    int r0 = tq * 4, m0 = (t - tq * tm) * 4;
-    T re[4][4], im[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) { re[u][v] = 0; im[u][v] = 0; }
-    for (int k = 0; k < K1; ++k) {
-      typename Vec4<T>::type sp = ld4(SP + k * Rp + r0), sm = ld4(SM + k * Rp + r0);
-      typename Vec4<T>::type c = ld4(CS + k * Mp + m0), sn = ld4(CS + (K1 + k) * Mp + m0);
-      T spv[4] = {sp.x, sp.y, sp.z, sp.w}, smv[4] = {sm.x, sm.y, sm.z, sm.w};
-      T cv[4] = {c.x, c.y, c.z, c.w}, sv[4] = {sn.x, sn.y, sn.z, sn.w};
+  // 2. phi DFT.  Fold the pairs (q, q') = (q, np/2 - q), q = 1..Qf, in place:
+  //    row q-1 <- x_q + x_q', row q'-1 <- x_q - x_q' (a self-paired middle row,
+  //    odd L, stays); even orders then read (SP+, SM-), odd orders (SP-, SM+).
+  for (int t = tid; t < (K1 / 2) * Rp; t += NT) {
+    int q = t / Rp + 1, r = t - (q - 1) * Rp, q2 = K1 + 1 - q;
+    T a = SP[(q - 1) * Rp + r], c = SP[(q2 - 1) * Rp + r];
+    SP[(q - 1) * Rp + r] = a + c; SP[(q2 - 1) * Rp + r] = a - c;
+    a = SM[(q - 1) * Rp + r]; c = SM[(q2 - 1) * Rp + r];
+    SM[(q - 1) * Rp + r] = a + c; SM[(q2 - 1) * Rp + r] = a - c;
+  }
+  __syncthreads();
+  //    4 x 4 tiles of (ring, 4 orders of one parity)
+  {
+    const int tr = Rp / 4, tc = Mq / 4;
+    const FastDiv dtc(2 * tc);
+    for (int t = tid; t < tr * 2 * tc; t += NT) {
+      int tq = dtc.div(t), rest = t - tq * 2 * tc;
+      int par = rest >= tc ? 1 : 0, c0 = (rest - par * tc) * 4, r0 = tq * 4;
+      const T *cst = CS + (2 * par) * Qf * Mq + c0, *snt = CS + (2 * par + 1) * Qf * Mq + c0;
+      T re[4][4], im[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
+        for (int v = 0; v < 4; ++v) { re[u][v] = 0; im[u][v] = 0; }
+      for (int q = 1; q <= Qf; ++q) {
+        const int rlo = q - 1, rhi = K1 - q;  // rows of x_q + x_q' and x_q - x_q'
+        typename Vec4<T>::type sp = ld4(SP + (par ? rhi : rlo) * Rp + r0);
+        typename Vec4<T>::type sm = ld4(SM + (par ? rlo : rhi) * Rp + r0);
+        typename Vec4<T>::type c = ld4(cst + (q - 1) * Mq), sn = ld4(snt + (q - 1) * Mq);
+        T spv[4] = {sp.x, sp.y, sp.z, sp.w}, smv[4] = {sm.x, sm.y, sm.z, sm.w};
+        T cv[4] = {c.x, c.y, c.z, c.w}, sv[4] = {sn.x, sn.y, sn.z, sn.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            re[u][v] = fma(spv[u], cv[v], re[u][v]);
+            im[u][v] = fma(-smv[u], sv[v], im[u][v]);
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        T e0 = E0[r0 + u], eh = EH[r0 + u];
+#pragma unroll
         for (int v = 0; v < 4; ++v) {
-          re[u][v] = fma(spv[u], cv[v], re[u][v]);
-          im[u][v] = fma(-smv[u], sv[v], im[u][v]);
+          int m = 2 * (c0 + v) + par;
+          if (m <= L) {
+            T *o = F + 2 * ((r0 + u) * Mp + m);
+            o[0] = re[u][v] + e0 + (par ? -eh : eh);
+            o[1] = im[u][v];
+          }
         }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      T e0 = E0[r0 + u], eh = EH[r0 + u];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        int m = m0 + v;
-        T* o = F + 2 * ((r0 + u) * Mp + m);
-        o[0] = re[u][v] + e0 + ((m & 1) ? -eh : eh);
-        o[1] = im[u][v];
       }
     }
   }
   __syncthreads();
-  // 3. Legendre: f_lm(r_s) = sum_j ptab[j][lm] F_m(s, j)
+  // 3. Legendre over the symmetric Gauss nodes: x_{nt-1-j} = -x_j and
+  //    Pbar_lm(-x) = (-1)^(l+m) Pbar_lm(x), so rows j and nt-1-j fold to
+  //    F(j) + F(nt-1-j) (even l+m, kept in row j) and F(j) - F(nt-1-j) (odd,
+  //    in row nt-1-j); the middle node of odd nt serves both.
+  const int Jh = (nt + 1) / 2;
+  for (int t = tid; t < Gs * (nt / 2) * (L + 1); t += NT) {
+    int m = t % (L + 1), gj = t / (L + 1), g = gj / (nt / 2), j = gj - g * (nt / 2);
+    T *fa = F + 2 * ((g * nt + j) * Mp + m), *fb = F + 2 * ((g * nt + nt - 1 - j) * Mp + m);
+    T ar = fa[0], ai = fa[1], br = fb[0], bi = fb[1];
+    fa[0] = ar + br; fa[1] = ai + bi;
+    fb[0] = ar - br; fb[1] = ai - bi;
+  }
+  __syncthreads();
   for (int lm = tid; lm < nlm; lm += NT) {
     int l = (int)((sqrtf(8.0f * lm + 1.0f) - 1.0f) * 0.5f);
     while (l * (l + 1) / 2 > lm) --l;
     while ((l + 1) * (l + 2) / 2 <= lm) ++l;
     int m = lm - l * (l + 1) / 2;
+    const bool odd = (l + m) & 1;
     T ar[G], ai[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) { ar[g] = 0; ai[g] = 0; }
-    const T *fj = F + 2 * m;
-    for (int j = 0; j < nt; ++j, fj += 2 * Mp) {
+    for (int j = 0; j < Jh; ++j) {
       T w = ptabT[(long)j * nlm + lm];
+      const T *fj = F + 2 * ((odd ? nt - 1 - j : j) * Mp + m);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const T *f = fj + 2 * g * nt * Mp;
@@ -300,7 +331,7 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
 template <typename T>
 size_t analyze2_smem(const Plan &p, int G) {
   int K1 = p.np / 2 - 1, Rp = (G * p.nt + 3) / 4 * 4;
-  return sizeof(T) * (2 * (size_t)K1 * Rp + 4 * (size_t)Rp + 2 * (size_t)K1 * p.Mp +
+  return sizeof(T) * (2 * (size_t)K1 * Rp + 4 * (size_t)Rp + 4 * (size_t)p.Qf * p.Mq +
                       2 * (size_t)Rp * p.Mp + 2 * (size_t)p.np);
 }
 
@@ -324,7 +355,7 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
                                                                                   : k_analyze2<T, 1>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<dim3(p.S / G, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj,
-                                                (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
+                                                (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp, p.Qf, p.Mq,
                                                 (const T *)p.ptab, coef);
       return cudaGetLastError();
     }

@@ -27,8 +27,9 @@ struct Plan {
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
   void *rcoef;                  // real, grouped layout: (a, -b, -e, 0) of the step l -> l+1
   void *seedK;                  // real [ngroups][4]: (sqrt(binom(2m, m+n)) of both halves, 0, 0)
-  void *dft_cs;                 // real [2][np/2-1][Mp]: cos, sin (2 pi m k / n_phi), k = 1..np/2-1
+  void *dft_cs;                 // real [2][2][Qf][Mq]: folded phi-DFT table (parity, cos|sin, q, column)
   int Mp;                       // orders padded to a multiple of 4
+  int Qf, Mq;                   // folded DFT rows ceil(L_J/2); columns per order parity, padded to 4
   int *pair_base;               // [npairs] first real of pair q in the grouped L_J layout
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 (SOFFT) layout
   // copy stream and events of matcha_align_host (created on first use)

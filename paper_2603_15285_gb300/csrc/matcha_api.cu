@@ -117,6 +117,8 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->npairs0 = (p->L0 + 1) * (p->L0 + 1);
   p->ns = 2 * p->K * (p->L0 + 1);
   p->Mp = (p->LJ + 1 + 3) / 4 * 4;
+  p->Qf = (p->LJ + 1) / 2;
+  p->Mq = (p->LJ / 2 + 1 + 3) / 4 * 4;
   p->ngroups = (p->LJ + 1) * (p->LJ + 2) / 2;
   p->nc = 2 * group_entries_host(p->LJ);
   p->nc0 = pair_entries_host(p->L0);
@@ -143,7 +145,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
   size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->ngroups);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
-  size_t o_dcs = add(rs * 2 * (size_t)(p->np / 2 - 1) * p->Mp);
+  size_t o_dcs = add(rs * 4 * (size_t)p->Qf * p->Mq);
   cudaError_t e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
   char *b = (char *)p->base;

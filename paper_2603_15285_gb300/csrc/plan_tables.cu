@@ -161,17 +161,22 @@ __global__ void k_soft_d(int L0, int ns, int npairs0, const int *pair_base, cons
   }
 }
 
-// Folded real DFT table: cs[0][k-1][m] = cos(2 pi m k / np), cs[1][k-1][m] =
-// sin(2 pi m k / np) for k = 1..np/2-1, m < Mp (zero for m > L).
-__global__ void k_dft_cs(int L, int Mp, double *cs) {
-  const int np = 2 * L + 2, K1 = np / 2 - 1;
+// Folded phi-DFT table.  With np = n_phi and k' = np/2 - k,
+//   cos(2 pi m k'/np) = (-1)^m cos(2 pi m k/np),
+//   sin(2 pi m k'/np) = (-1)^(m+1) sin(2 pi m k/np),
+// so the sums over k = 1..np/2-1 fold onto q = 1..Qf.  Entry
+// cs[p][0][q-1][c] = cos(2 pi m q / np), cs[p][1][q-1][c] = sin(2 pi m q / np)
+// for the order m = 2c + p of parity p (zero for m > L).
+__global__ void k_dft_cs(int L, int Qf, int Mq, double *cs) {
+  const int np = 2 * L + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= K1 * Mp) return;
-  int k = t / Mp + 1, m = t % Mp;
+  if (t >= 2 * Qf * Mq) return;
+  int p = t / (Qf * Mq), rem = t - p * Qf * Mq, q = rem / Mq + 1, c = rem - (q - 1) * Mq;
+  int m = 2 * c + p;
   double sv = 0.0, cv = 0.0;
-  if (m <= L) sincospi(2.0 * ((long)m * k % np) / np, &sv, &cv);
-  cs[t] = cv;
-  cs[K1 * Mp + t] = sv;
+  if (m <= L) sincospi(2.0 * ((long)m * q % np) / np, &sv, &cv);
+  cs[(2 * p) * Qf * Mq + rem] = cv;
+  cs[(2 * p + 1) * Qf * Mq + rem] = sv;
 }
 
 __global__ void k_to_float(const double *in, float *out, long n) {
@@ -183,7 +188,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
   size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.ngroups;
-  size_t n_dcs = 2 * (size_t)(p.np / 2 - 1) * p.Mp;
+  size_t n_dcs = 4 * (size_t)p.Qf * p.Mq;
   double *gx, *gw;
   cudaError_t e;
   if ((e = cudaMalloc(&gx, sizeof(double) * 2 * p.S))) return e;
@@ -208,7 +213,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   k_twiddle<<<(p.ns + 127) / 128, 128, 0, st>>>(p.ns, tw);
   k_rcoef<<<p.npairs, 64, 0, st>>>(p.LJ, p.npairs, p.pair_base, rc);
   k_seedK<<<(p.ngroups + 127) / 128, 128, 0, st>>>(p.ngroups, K);
-  k_dft_cs<<<(unsigned)((n_dcs / 2 + 127) / 128), 128, 0, st>>>(p.LJ, p.Mp, dcs);
+  k_dft_cs<<<(unsigned)((n_dcs / 2 + 127) / 128), 128, 0, st>>>(p.LJ, p.Qf, p.Mq, dcs);
   k_soft_d<<<dim3(p.npairs0, p.ns), 32, 0, st>>>(p.L0, p.ns, p.npairs0, p.pair_base, p.pair_off0,
                                                  rc, K, p.nc0, sd);
   if (!p.fp64) {
