@@ -86,6 +86,7 @@ template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st);
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
+bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
 cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
                                 const double *cand_euler, const double *cand_score,
                                 const int *cand_flags, double *euler, double *R, double *score,

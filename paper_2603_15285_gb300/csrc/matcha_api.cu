@@ -51,7 +51,8 @@ size_t carve_align(const Plan &p, int B, int Bt, char *base, AlignWs *w) {
   w->f = cv.take<char>(rs * coefv * B);
   w->h = cv.take<char>(rs * coefv * Bt);
   w->c = cv.take<char>(rs * 4 * (size_t)p.nc * B);
-  w->grid = cv.take<char>(rs * (size_t)p.ns * p.ns * p.ns * B);
+  // the grid itself is only materialised when no fused SOFFT kernel applies
+  w->grid = soft_grid_optional(p) ? nullptr : cv.take<char>(rs * (size_t)p.ns * p.ns * p.ns * B);
   w->cidx = cv.take<int>((size_t)B * p.P);
   w->cflags = cv.take<int>((size_t)B * p.P);
   w->ncand = cv.take<int>(B);
@@ -309,9 +310,15 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   if ((s = matcha_analyze(plan, particles, B, w.f, stream))) return s;
   if ((s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
   if ((s = matcha_correlate_coeffs(plan, w.f, w.h, B, tstride, w.c, stream))) return s;
-  if ((s = matcha_soft_search(plan, w.c, B, P_per, w.grid, w.cidx, w.ceuler, w.cscore, w.ncand,
-                              stream)))
-    return s;
+  {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = p->fp64 ? launch_soft<double>(*p, (const double *)w.c, B, P_per,
+                                                  (double *)w.grid, w.cidx, w.ceuler, w.cscore,
+                                                  w.ncand, st)
+                            : launch_soft<float>(*p, (const float *)w.c, B, P_per, (float *)w.grid,
+                                                 w.cidx, w.ceuler, w.cscore, w.ncand, st);
+    if (e != cudaSuccess) return fail_cuda(e, "soft_search");
+  }
   if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags, nullptr,
                                stream)))
     return s;

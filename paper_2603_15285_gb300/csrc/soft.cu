@@ -84,6 +84,11 @@ k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restr
   }
 }
 
+// max(a, b) that returns NaN when either is NaN
+template <typename T> __device__ __forceinline__ T nan_max(T a, T b) {
+  return (a != a || a > b) ? a : b;
+}
+
 template <typename T>
 __device__ __forceinline__ bool precedes(T va, int ia, T vb, int ib) {
   return va > vb || (va == vb && ia < ib);
@@ -638,7 +643,8 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
   // every section starts on a multiple of 4 elements (16-byte vector loads)
   auto al4 = [](long x) { return (x + 3) & ~3L; };
   T *ring = reinterpret_cast<T *>(smem_raw);   // [NR][n2]
-  T *Sg = ring + al4(NR * n2);                  // [KB+1][W*W] complex
+  T *mx = ring + al4(NR * n2);                  // [NR][n2] 3x3 (alpha, gamma) maxima
+  T *Sg = mx + al4(NR * n2);                    // [KB+1][W*W] complex
   const int nsp = (ns + 3) / 4 * 4, nq4 = nsp / 4;
   T *G = Sg + al4((KB + 1) * 2 * W * W);        // [KB+1][L0+1][re|im][nsp]
   T *Eg = G + al4((KB + 1) * 2 * (L0 + 1) * nsp);  // [W][nsp] complex: e^{i n g_j}
@@ -765,6 +771,21 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
         for (int v = 0; v < 4; ++v)
           if (i0 + u < ns && j0 + v < ns) dst[(i0 + u) * ns + j0 + v] = o[u][v];
     }
+    __syncthreads();
+    // 3x3 maxima over (alpha, gamma), both wrapping, of the new slices;
+    // a NaN anywhere in the window makes the maximum NaN
+    for (int t = tid; t < nk * n2; t += NT) {
+      int kk = dn2.div(t), r = t - kk * n2;
+      int i = dns.div(r), j = r - i * ns;
+      const T *sl = ring + ((ka + kk) % NR) * n2;
+      const int im = (i == 0 ? ns - 1 : i - 1) * ns, ic = i * ns, ip = (i == ns - 1 ? 0 : i + 1) * ns;
+      const int jm = j == 0 ? ns - 1 : j - 1, jp = j == ns - 1 ? 0 : j + 1;
+      T m = sl[ic + j];
+      m = nan_max(m, sl[ic + jm]); m = nan_max(m, sl[ic + jp]);
+      m = nan_max(m, sl[im + jm]); m = nan_max(m, sl[im + j]); m = nan_max(m, sl[im + jp]);
+      m = nan_max(m, sl[ip + jm]); m = nan_max(m, sl[ip + j]); m = nan_max(m, sl[ip + jp]);
+      mx[((ka + kk) % NR) * n2 + r] = m;
+    }
     done = hi;
     if (tid == 0) counters[0] = 0;
     __syncthreads();
@@ -783,7 +804,13 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
       int i = dns.div(r), j = r - i * ns;
       int p = (i * ns + k) * ns + j;
       T v = ring[(k % NR) * n2 + r];
-      bool ok = v == v;
+      // the 3x3x3 maximum (slices outside the beta range skipped) rules out
+      // every point below it; a point equal to it takes the exact test, which
+      // also orders equal values by index
+      T m3 = mx[(k % NR) * n2 + r];
+      if (k > 0) m3 = nan_max(m3, mx[((k - 1) % NR) * n2 + r]);
+      if (k < ns - 1) m3 = nan_max(m3, mx[((k + 1) % NR) * n2 + r]);
+      bool ok = v == m3;
       for (int dk = -1; dk <= 1 && ok; ++dk) {
         int kq = k + dk;
         if (kq < 0 || kq >= ns) continue;
@@ -856,7 +883,7 @@ size_t soft_chunk_smem(const Plan &p, size_t ts) {
   size_t capc = (size_t)SOFT_KB * ((p.ns + 1) / 2) * ((p.ns + 1) / 2);
   size_t nsp = (size_t)(p.ns + 3) / 4 * 4;
   auto al4 = [](size_t x) { return (x + 3) & ~size_t(3); };
-  return ts * (al4((SOFT_KB + 2) * n2) + al4((SOFT_KB + 1) * 2 * W * W) +
+  return ts * (2 * al4((SOFT_KB + 2) * n2) + al4((SOFT_KB + 1) * 2 * W * W) +
                al4((SOFT_KB + 1) * 2 * (size_t)(p.L0 + 1) * nsp) + al4(2 * W * nsp) +
                al4(2 * (size_t)(p.L0 + 1) * nsp) + 4 * (size_t)p.nc0 + capc + 32) +
          sizeof(int) * (capc + 32 + 4) + 16;
@@ -866,6 +893,14 @@ size_t soft_stream_smem(const Plan &p, size_t ts) {
   size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns, capc = (size_t)((p.ns + 1) / 2) * ((p.ns + 1) / 2);
   return ts * (3 * n2 + 2 * W * W + 2 * (size_t)(p.L0 + 1) * p.ns + capc + 32) +
          sizeof(int) * (capc + 32 + 4) + 32 + ts * 4 * (size_t)p.nc0;
+}
+
+// True when one of the fused kernels (chunked, streaming or FP32 fused) serves
+// the plan, so the full grid need not be materialised.
+bool soft_grid_optional(const Plan &p) {
+  const size_t ts = p.fp64 ? 8 : 4;
+  return soft_chunk_smem(p, ts) <= 227 * 1024 - 1024 || soft_stream_smem(p, ts) <= 227 * 1024 - 1024 ||
+         (!p.fp64 && soft_fused_ok(p));
 }
 
 template <typename T>
