@@ -23,61 +23,72 @@ __device__ __forceinline__ void coef_at(const T *__restrict__ f, int nlm, int s,
 
 // One CTA per (particle, degree pair {l, L-l}): the coefficients of both
 // degrees (all shells, orders 0..l) are staged in shared memory with the
-// template side pre-multiplied by the radial weight, then one thread per order
-// pair (m, n), m >= |n|, produces (c^l_mn, c^l_nm).  Pairing degree l with
-// L - l balances the (l+1)^2 work of a degree.
+// template side pre-multiplied by the radial weight, then one thread per
+// (degree, order pair (m, n), m >= |n|) produces (c^l_mn, c^l_nm); the two
+// degrees share one item loop, so pairing l with L - l balances the
+// (l+1)^2 + (L-l+1)^2 items of a CTA.  The signs of the negative order -|n|
+// are applied once after the shell sums.
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, long h_stride,
                 const double *__restrict__ wrad, const int *__restrict__ pair_base, long nc,
                 T *__restrict__ c) {
+  using C2 = typename Cplx<T>::type;
   const long b = blockIdx.y;
   const int nlm = (L + 1) * (L + 2) / 2;
   const T *fb = f + 2 * b * (long)S * nlm;
   const T *hb = h + 2 * (b * h_stride) * (long)S * nlm;
   T *cb = c + 4 * b * nc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sF = reinterpret_cast<T *>(smem_raw);
+  C2 *sF = reinterpret_cast<C2 *>(smem_raw);
   const int l_lo = blockIdx.x, l_hi = L - blockIdx.x;
-  for (int pass = 0; pass < 2; ++pass) {
-    const int l = pass ? l_hi : l_lo;
-    if (pass && l_hi == l_lo) break;
-    const int no = l + 1;                    // orders 0..l
-    T *Fs = sF;                              // [S][no] complex
-    T *Hs = sF + 2 * S * no;                 // [S][no] complex, times w_s
-    const int base = l * (l + 1) / 2;
+  const int npass = l_hi == l_lo ? 1 : 2;
+  // stage: degree d's orders 0..l at [S][l+1] (F) and [S][l+1] (w H)
+  const int no0 = l_lo + 1, no1 = l_hi + 1;
+  C2 *F0 = sF, *H0 = sF + S * no0, *F1 = sF + 2 * S * no0, *H1 = F1 + S * no1;
+  for (int d = 0; d < npass; ++d) {
+    const int l = d ? l_hi : l_lo, no = l + 1, base = l * (l + 1) / 2;
+    C2 *Fd = d ? F1 : F0, *Hd = d ? H1 : H0;
     for (int t = threadIdx.x; t < S * no; t += blockDim.x) {
       int s = t / no, m = t - s * no;
       long src = 2 * ((long)s * nlm + base + m);
       T w = (T)wrad[s];
-      Fs[2 * t] = fb[src]; Fs[2 * t + 1] = fb[src + 1];
-      Hs[2 * t] = w * hb[src]; Hs[2 * t + 1] = w * hb[src + 1];
+      C2 fv, hv;
+      fv.x = fb[src]; fv.y = fb[src + 1];
+      hv.x = w * hb[src]; hv.y = w * hb[src + 1];
+      Fd[t] = fv; Hd[t] = hv;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < no * no; q += blockDim.x) {
-      int m = isqrt_floor(q), n = q - m * m - m;
-      int an = n < 0 ? -n : n;
-      // order -|n| of a real function: (-1)^n conj(.)
-      T sr = (n < 0 && (an & 1)) ? T(-1) : T(1);
-      T si = n < 0 ? -sr : sr;
-      T r1 = 0, i1 = 0, r2 = 0, i2 = 0;
-      for (int s = 0; s < S; ++s) {
-        const T *F = Fs + 2 * s * no, *H = Hs + 2 * s * no;
-        T fmr = F[2 * m], fmi = F[2 * m + 1];
-        T hmr = H[2 * m], hmi = H[2 * m + 1];
-        T fnr = sr * F[2 * an], fni = si * F[2 * an + 1];
-        T hnr = sr * H[2 * an], hni = si * H[2 * an + 1];
-        // c_mn += f_lm conj(w h_ln);  c_nm += f_ln conj(w h_lm)
-        r1 = fma(fmr, hnr, fma(fmi, hni, r1));
-        i1 = fma(fmi, hnr, fma(-fmr, hni, i1));
-        r2 = fma(fnr, hmr, fma(fni, hmi, r2));
-        i2 = fma(fni, hmr, fma(-fnr, hmi, i2));
-      }
-      T *o = cb + pair_base[q] + 8L * (l - m);
-      o[0] = r1; o[2] = i1; o[4] = r2; o[6] = i2;
-      if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }  // empty partner
+  }
+  __syncthreads();
+  const int n_lo = (l_lo + 1) * (l_lo + 1), n_tot = n_lo + (npass == 2 ? (l_hi + 1) * (l_hi + 1) : 0);
+  for (int t = threadIdx.x; t < n_tot; t += blockDim.x) {
+    const int d = t < n_lo ? 0 : 1, q = d ? t - n_lo : t, l = d ? l_hi : l_lo, no = l + 1;
+    const int m = isqrt_floor(q), n = q - m * m - m;
+    const int an = n < 0 ? -n : n;
+    // order -|n| of a real function: f_{l,-|n|} = (-1)^|n| conj(f_{l,|n|})
+    const T sr = (n < 0 && (an & 1)) ? T(-1) : T(1);
+    const T si = n < 0 ? -sr : sr;
+    // c_mn = sum_s f_lm conj(w h_ln), c_nm = sum_s f_ln conj(w h_lm), with the
+    // order-n factors' signs (sr, si) taken out of the sums
+    T a = 0, bb = 0, cc = 0, dd = 0, e = 0, g = 0, ii = 0, jj = 0;
+    const C2 *F = d ? F1 : F0, *H = d ? H1 : H0;
+    for (int s = 0; s < S; ++s, F += no, H += no) {
+      const C2 fm = F[m], hm = H[m], fn = F[an], hn = H[an];
+      a = fma(fm.x, hn.x, a);  bb = fma(fm.y, hn.y, bb);
+      cc = fma(fm.y, hn.x, cc); dd = fma(fm.x, hn.y, dd);
+      e = fma(fn.x, hm.x, e);  g = fma(fn.y, hm.y, g);
+      ii = fma(fn.y, hm.x, ii); jj = fma(fn.x, hm.y, jj);
     }
-    __syncthreads();
+    T *o = cb + pair_base[q] + 8L * (l - m);
+    o[0] = sr * a + si * bb;   // Re c_mn
+    o[2] = sr * cc - si * dd;  // Im c_mn
+    o[4] = sr * e + si * g;    // Re c_nm
+    o[6] = si * ii - sr * jj;  // Im c_nm
+    if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }  // empty partner
   }
 }
 
@@ -85,7 +96,7 @@ template <typename T>
 cudaError_t launch_correlate(const Plan &p, const T *f, const T *h, int B, int hstride, T *c,
                              cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  size_t smem = sizeof(T) * 4 * (size_t)p.S * (p.LJ + 1);
+  size_t smem = sizeof(T) * 4 * (size_t)p.S * (p.LJ + 2);  // both degrees of a pair
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {
     cudaFuncSetAttribute(k_correlate_deg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -85,7 +85,12 @@ k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restr
 }
 
 // max(a, b) that returns NaN when either is NaN
-template <typename T> __device__ __forceinline__ T nan_max(T a, T b) {
+__device__ __forceinline__ float nan_max(float a, float b) {
+  float d;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ double nan_max(double a, double b) {
   return (a != a || a > b) ? a : b;
 }
 
@@ -773,18 +778,22 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
     }
     __syncthreads();
     // 3x3 maxima over (alpha, gamma), both wrapping, of the new slices;
-    // a NaN anywhere in the window makes the maximum NaN
-    for (int t = tid; t < nk * n2; t += NT) {
-      int kk = dn2.div(t), r = t - kk * n2;
-      int i = dns.div(r), j = r - i * ns;
-      const T *sl = ring + ((ka + kk) % NR) * n2;
+    // a NaN anywhere in the window makes the maximum NaN.  A thread keeps one
+    // (alpha, gamma) position and walks the slices.
+    for (int r = tid; r < n2; r += NT) {
+      const int i = dns.div(r), j = r - i * ns;
       const int im = (i == 0 ? ns - 1 : i - 1) * ns, ic = i * ns, ip = (i == ns - 1 ? 0 : i + 1) * ns;
       const int jm = j == 0 ? ns - 1 : j - 1, jp = j == ns - 1 ? 0 : j + 1;
-      T m = sl[ic + j];
-      m = nan_max(m, sl[ic + jm]); m = nan_max(m, sl[ic + jp]);
-      m = nan_max(m, sl[im + jm]); m = nan_max(m, sl[im + j]); m = nan_max(m, sl[im + jp]);
-      m = nan_max(m, sl[ip + jm]); m = nan_max(m, sl[ip + j]); m = nan_max(m, sl[ip + jp]);
-      mx[((ka + kk) % NR) * n2 + r] = m;
+      int slot = ka % NR;
+      for (int kk = 0; kk < nk; ++kk) {
+        const T *sl = ring + slot * n2;
+        T m = sl[ic + j];
+        m = nan_max(m, sl[ic + jm]); m = nan_max(m, sl[ic + jp]);
+        m = nan_max(m, sl[im + jm]); m = nan_max(m, sl[im + j]); m = nan_max(m, sl[im + jp]);
+        m = nan_max(m, sl[ip + jm]); m = nan_max(m, sl[ip + j]); m = nan_max(m, sl[ip + jp]);
+        mx[slot * n2 + r] = m;
+        slot = slot == NR - 1 ? 0 : slot + 1;
+      }
     }
     done = hi;
     if (tid == 0) counters[0] = 0;
@@ -798,36 +807,42 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
         go[((long)i * ns + k) * ns + j] = ring[(k % NR) * n2 + r];
       }
     }
-    // local maxima of slices k0..k1-1
-    for (int t = tid; t < nt_ * n2; t += NT) {
-      int kk = dn2.div(t), r = t - kk * n2, k = k0 + kk;
-      int i = dns.div(r), j = r - i * ns;
-      int p = (i * ns + k) * ns + j;
-      T v = ring[(k % NR) * n2 + r];
-      // the 3x3x3 maximum (slices outside the beta range skipped) rules out
-      // every point below it; a point equal to it takes the exact test, which
-      // also orders equal values by index
-      T m3 = mx[(k % NR) * n2 + r];
-      if (k > 0) m3 = nan_max(m3, mx[((k - 1) % NR) * n2 + r]);
-      if (k < ns - 1) m3 = nan_max(m3, mx[((k + 1) % NR) * n2 + r]);
-      bool ok = v == m3;
-      for (int dk = -1; dk <= 1 && ok; ++dk) {
-        int kq = k + dk;
-        if (kq < 0 || kq >= ns) continue;
-        const T *sl = ring + (kq % NR) * n2;
-        for (int di = -1; di <= 1 && ok; ++di) {
-          int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
-          for (int dj = -1; dj <= 1; ++dj) {
-            if (!di && !dk && !dj) continue;
-            int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
-            int q = (ii * ns + kq) * ns + jj;
-            if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+    // local maxima of slices k0..k1-1: the 3x3x3 maximum (slices outside the
+    // beta range skipped) rules out every point below it; a point equal to it
+    // takes the exact test, which also orders equal values by index
+    for (int r = tid; r < n2; r += NT) {
+      int slot = k0 % NR;
+      int prev = slot == 0 ? NR - 1 : slot - 1;
+      T mprev = k0 > 0 ? mx[prev * n2 + r] : T(-INFINITY), mcur = mx[slot * n2 + r];
+      for (int k = k0; k < k1; ++k) {
+        const int next = slot == NR - 1 ? 0 : slot + 1;
+        const T mnext = k < ns - 1 ? mx[next * n2 + r] : T(-INFINITY);
+        const T v = ring[slot * n2 + r];
+        const T m3 = nan_max(nan_max(mprev, mcur), mnext);
+        if (v == m3) {
+          const int i = dns.div(r), j = r - i * ns;
+          const int p = (i * ns + k) * ns + j;
+          bool ok = true;
+          for (int dk = -1; dk <= 1 && ok; ++dk) {
+            int kq = k + dk;
+            if (kq < 0 || kq >= ns) continue;
+            const T *sl = ring + (kq % NR) * n2;
+            for (int di = -1; di <= 1 && ok; ++di) {
+              int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+              for (int dj = -1; dj <= 1; ++dj) {
+                if (!di && !dk && !dj) continue;
+                int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+                int q = (ii * ns + kq) * ns + jj;
+                if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+              }
+            }
+          }
+          if (ok) {
+            int pos = atomicAdd(&counters[0], 1);
+            if (pos < capc) { cv[pos] = v; ci[pos] = p; }
           }
         }
-      }
-      if (ok) {
-        int pos = atomicAdd(&counters[0], 1);
-        if (pos < capc) { cv[pos] = v; ci[pos] = p; }
+        mprev = mcur; mcur = mnext; slot = next;
       }
     }
     __syncthreads();
