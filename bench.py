@@ -215,7 +215,9 @@ def main():
                flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
     H = plan.handle
     stages = ["analyze", "correlate", "soft", "newton", "select"]
-    KERNELS_PER_STEP = 7  # analyze x2, correlate, soft grid, top-P, newton, final select
+    # k_analyze2 x2 (particles, templates), k_correlate_deg, k_soft_chunk (grid and top-P
+    # fused), k_newton, k_final_select
+    KERNELS_PER_STEP = 6
 
     def step(ev=None):
         def mark(i):
@@ -352,7 +354,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.max_threads()
-        nb = min(B, 2 * cores)
+        nb = min(B, 5 * cores)
         kw = dict(S=w.n_shells, r_max=w.r_max, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter,
                   L_sched=w.L_sched)
         pc, tc = parts[:nb].cpu().numpy(), temps[:nb].cpu().numpy()

@@ -16,7 +16,7 @@
  *   - `*_dev` pointers are device memory owned by the caller; the library never
  *     allocates or frees in those calls (only plan create/destroy do);
  *   - precision: a plan computes either in FP64 throughout (MATCHA_FP64) or
- *     in FP32 with FP64 angles, 3x3 solves and final comparisons (MATCHA_FP32);
+ *     in FP32 with FP64 angles, acceptance tests and final comparisons (MATCHA_FP32);
  *     "real" below is double for FP64 plans and float for FP32 plans, and a
  *     complex number is two consecutive reals (re, im);
  *   - volumes: float32, C order [z][y][x], N^3 per volume, voxel [k][j][i] at
