@@ -64,31 +64,72 @@ k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, 
     }
   }
   __syncthreads();
-  const int n_lo = (l_lo + 1) * (l_lo + 1), n_tot = n_lo + (npass == 2 ? (l_hi + 1) * (l_hi + 1) : 0);
-  for (int t = threadIdx.x; t < n_tot; t += blockDim.x) {
-    const int d = t < n_lo ? 0 : 1, q = d ? t - n_lo : t, l = d ? l_hi : l_lo, no = l + 1;
-    const int m = isqrt_floor(q), n = q - m * m - m;
-    const int an = n < 0 ? -n : n;
-    // order -|n| of a real function: f_{l,-|n|} = (-1)^|n| conj(f_{l,|n|})
-    const T sr = (n < 0 && (an & 1)) ? T(-1) : T(1);
-    const T si = n < 0 ? -sr : sr;
-    // c_mn = sum_s f_lm conj(w h_ln), c_nm = sum_s f_ln conj(w h_lm), with the
-    // order-n factors' signs (sr, si) taken out of the sums
-    T a = 0, bb = 0, cc = 0, dd = 0, e = 0, g = 0, ii = 0, jj = 0;
+  // Products over the shells for every order pair (a, b), 0 <= a, b <= l:
+  //   A = sum f_a.re h_b.re, B = sum f_a.im h_b.im, C = sum f_a.im h_b.re, D = sum f_a.re h_b.im,
+  // so that P1 = sum f_a conj(h_b) = (A + B) + i (C - D) and P2 = sum f_a h_b =
+  // (A - B) + i (C + D).  With f_{l,-k} = (-1)^k conj(f_{lk}) (real volumes):
+  //   c_mn = P1[m][n] (n >= 0),  (-1)^|n| P2[m][|n|] (n < 0),
+  //   c_nm = P1[n][m] (n >= 0),  (-1)^|n| conj(P2[|n|][m]) (n < 0).
+  // One thread per 2 x 2 block of (a, b): two 128-bit loads per shell feed 16
+  // multiply-adds.
+  const int h0 = (l_lo + 2) / 2, h1 = (l_hi + 2) / 2;  // blocks per side
+  const int t_lo = h0 * h0, t_tot = t_lo + (npass == 2 ? h1 * h1 : 0);
+  for (int t = threadIdx.x; t < t_tot; t += blockDim.x) {
+    const int d = t < t_lo ? 0 : 1, tt = d ? t - t_lo : t, hh = d ? h1 : h0;
+    const int l = d ? l_hi : l_lo, no = l + 1;
+    const int a0 = 2 * (tt / hh), b0 = 2 * (tt - (tt / hh) * hh);
+    // rows past l read a zero-weighted copy of row l (loaded, never stored)
+    const int a1 = a0 + 1 <= l ? a0 + 1 : a0, b1 = b0 + 1 <= l ? b0 + 1 : b0;
+    T acc[2][2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[u][v][k] = 0;
     const C2 *F = d ? F1 : F0, *H = d ? H1 : H0;
     for (int s = 0; s < S; ++s, F += no, H += no) {
-      const C2 fm = F[m], hm = H[m], fn = F[an], hn = H[an];
-      a = fma(fm.x, hn.x, a);  bb = fma(fm.y, hn.y, bb);
-      cc = fma(fm.y, hn.x, cc); dd = fma(fm.x, hn.y, dd);
-      e = fma(fn.x, hm.x, e);  g = fma(fn.y, hm.y, g);
-      ii = fma(fn.y, hm.x, ii); jj = fma(fn.x, hm.y, jj);
+      const C2 fa[2] = {F[a0], F[a1]}, hb[2] = {H[b0], H[b1]};
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          acc[u][v][0] = fma(fa[u].x, hb[v].x, acc[u][v][0]);
+          acc[u][v][1] = fma(fa[u].y, hb[v].y, acc[u][v][1]);
+          acc[u][v][2] = fma(fa[u].y, hb[v].x, acc[u][v][2]);
+          acc[u][v][3] = fma(fa[u].x, hb[v].y, acc[u][v][3]);
+        }
     }
-    T *o = cb + pair_base[q] + 8L * (l - m);
-    o[0] = sr * a + si * bb;   // Re c_mn
-    o[2] = sr * cc - si * dd;  // Im c_mn
-    o[4] = sr * e + si * g;    // Re c_nm
-    o[6] = si * ii - sr * jj;  // Im c_nm
-    if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }  // empty partner
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int ai = a0 + u, bi = b0 + v;
+        if (ai > l || bi > l) continue;
+        const T A = acc[u][v][0], B = acc[u][v][1], C = acc[u][v][2], D = acc[u][v][3];
+        const T p1r = A + B, p1i = C - D, p2r = A - B, p2i = C + D;
+        // P1[ai][bi]: c_mn of pair (ai, bi) when ai >= bi; c_nm of pair (bi, ai) when ai <= bi
+        if (ai >= bi) {
+          const int m = ai, n = bi, q = m * m + n + m;
+          T *o = cb + pair_base[q] + 8L * (l - m);
+          o[0] = p1r; o[2] = p1i;
+          if (n == m) { o[4] = p1r; o[6] = p1i; o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }
+        }
+        if (ai < bi) {
+          const int m = bi, n = ai, q = m * m + n + m;
+          T *o = cb + pair_base[q] + 8L * (l - m);
+          o[4] = p1r; o[6] = p1i;
+        }
+        // P2[ai][bi] with the smaller index k > 0 as |n|: pair (max, -min)
+        const int mx = ai > bi ? ai : bi, k = ai > bi ? bi : ai;
+        if (k > 0) {
+          const T sg = (k & 1) ? T(-1) : T(1);
+          const int q = mx * mx - k + mx;
+          T *o = cb + pair_base[q] + 8L * (l - mx);
+          if (ai >= bi) { o[0] = sg * p2r; o[2] = sg * p2i; }    // c_{m,-k} = (-1)^k P2[m][k]
+          if (ai <= bi) { o[4] = sg * p2r; o[6] = -sg * p2i; }   // c_{-k,m} = (-1)^k conj(P2[k][m])
+        }
+      }
   }
 }
 
