@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256)
 k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const double *__restrict__ rs, const double *__restrict__ xj, const T *__restrict__ phi_cs,
            const T *__restrict__ dcs, int Mp, int Qf, int Mq, const T *__restrict__ ptabT,
-           T *__restrict__ out) {
+           const T *__restrict__ ring, T *__restrict__ out) {
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
   const int Gs = G;  // the launcher picks G dividing S
@@ -160,13 +160,11 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     E0[t] = 0; EH[t] = 0;
     for (int k = 0; k < K1; ++k) { SP[k * Rp + t] = 0; SM[k * Rp + t] = 0; }
   }
-  // per-ring constants: rho = r_s sin(t_j), z = c0 + r_s cos(t_j)
-  const FastDiv dnt(nt), dhalf(half);
+  // per-ring constants from the plan: rho = r_s sin(t_j), z = c0 + r_s cos(t_j)
+  const FastDiv dhalf(half);
   for (int r = tid; r < R; r += NT) {
-    int sl = dnt.div(r), j = r - sl * nt;
-    double rr = rs[s0 + sl], x = xj[j];
-    RH[r] = (T)(rr * sqrt(fmax(1.0 - x * x, 0.0)));
-    RZ[r] = (T)(0.5 * N + rr * x);
+    RH[r] = ring[2 * ((long)s0 * nt + r)];
+    RZ[r] = ring[2 * ((long)s0 * nt + r) + 1];
   }
   for (int t = tid; t < 2 * np; t += NT) PH[t] = phi_cs[t];
   __syncthreads();
@@ -355,8 +353,9 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
                                                                                   : k_analyze2<T, 1>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<dim3(p.S / G, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj,
-                                                (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp, p.Qf, p.Mq,
-                                                (const T *)p.ptab, coef);
+                                                (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
+                                                p.Qf, p.Mq, (const T *)p.ptab, (const T *)p.ring,
+                                                coef);
       return cudaGetLastError();
     }
   }

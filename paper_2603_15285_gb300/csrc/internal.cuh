@@ -30,6 +30,7 @@ struct Plan {
   void *dft_cs;                 // real [2][2][Qf][Mq]: folded phi-DFT table (parity, cos|sin, q, column)
   int Mp;                       // orders padded to a multiple of 4
   int Qf, Mq;                   // folded DFT rows ceil(L_J/2); columns per order parity, padded to 4
+  void *ring;                   // real [S * nt][2]: (r_s sin t_j, N/2 + r_s cos t_j) of ring s * nt + j
   int *pair_base;               // [npairs] first real of pair q in the grouped L_J layout
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 (SOFFT) layout
   // copy stream and events of matcha_align_host (created on first use)

@@ -147,6 +147,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->ngroups);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
   size_t o_dcs = add(rs * 4 * (size_t)p->Qf * p->Mq);
+  size_t o_ring = add(rs * 2 * (size_t)p->S * p->nt);
   cudaError_t e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
   char *b = (char *)p->base;
@@ -156,6 +157,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->rcoef = b + o_rc; p->seedK = b + o_K;
   p->pair_base = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
   p->dft_cs = b + o_dcs;
+  p->ring = b + o_ring;
   e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = build_tables(*p, 0);

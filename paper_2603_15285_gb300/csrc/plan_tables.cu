@@ -179,6 +179,17 @@ __global__ void k_dft_cs(int L, int Qf, int Mq, double *cs) {
   cs[(2 * p + 1) * Qf * Mq + rem] = sv;
 }
 
+// Ring constants of the shell sampling: ring r = s * nt + j lies in the plane
+// z = N/2 + r_s cos t_j with radius r_s sin t_j.
+__global__ void k_ring(int S, int nt, int N, const double *rs, const double *xj, double *ring) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= S * nt) return;
+  int s = r / nt, j = r - s * nt;
+  double rr = rs[s], x = xj[j];
+  ring[2 * r] = rr * sqrt(fmax(1.0 - x * x, 0.0));
+  ring[2 * r + 1] = 0.5 * N + rr * x;
+}
+
 __global__ void k_to_float(const double *in, float *out, long n) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -188,7 +199,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
   size_t n_softd = (size_t)p.ns * p.nc0, n_rc = 4 * (size_t)p.nc, n_K = 4 * (size_t)p.ngroups;
-  size_t n_dcs = 4 * (size_t)p.Qf * p.Mq;
+  size_t n_dcs = 4 * (size_t)p.Qf * p.Mq, n_ring = 2 * (size_t)p.S * p.nt;
   double *gx, *gw;
   cudaError_t e;
   if ((e = cudaMalloc(&gx, sizeof(double) * 2 * p.S))) return e;
@@ -197,7 +208,7 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   k_radial<<<(p.S + 63) / 64, 64, 0, st>>>(p.S, p.R, gx, gw, p.rs, p.wrad);
   k_gauss_legendre<<<(p.nt + 63) / 64, 64, 0, st>>>(p.nt, p.xj, p.wj);
   double *d64 = nullptr;
-  size_t tot = n_ptab + n_phi + n_tw + n_softd + n_rc + n_K + n_dcs;
+  size_t tot = n_ptab + n_phi + n_tw + n_softd + n_rc + n_K + n_dcs + n_ring;
   if (!p.fp64) {
     if ((e = cudaMalloc(&d64, sizeof(double) * tot))) { cudaFree(gx); return e; }
   }
@@ -208,19 +219,21 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
   double *rc = p.fp64 ? (double *)p.rcoef : sd + n_softd;
   double *K = p.fp64 ? (double *)p.seedK : rc + n_rc;
   double *dcs = p.fp64 ? (double *)p.dft_cs : K + n_K;
+  double *ring = p.fp64 ? (double *)p.ring : dcs + n_dcs;
   k_ptab<<<(unsigned)((n_ptab + 127) / 128), 128, 0, st>>>(p.LJ, p.nt, p.np, p.xj, p.wj, ptab);
   k_twiddle<<<(p.np + 127) / 128, 128, 0, st>>>(p.np, phi);
   k_twiddle<<<(p.ns + 127) / 128, 128, 0, st>>>(p.ns, tw);
   k_rcoef<<<p.npairs, 64, 0, st>>>(p.LJ, p.npairs, p.pair_base, rc);
   k_seedK<<<(p.ngroups + 127) / 128, 128, 0, st>>>(p.ngroups, K);
   k_dft_cs<<<(unsigned)((n_dcs / 2 + 127) / 128), 128, 0, st>>>(p.LJ, p.Qf, p.Mq, dcs);
+  k_ring<<<(unsigned)((n_ring / 2 + 127) / 128), 128, 0, st>>>(p.S, p.nt, p.N, p.rs, p.xj, ring);
   k_soft_d<<<dim3(p.npairs0, p.ns), 32, 0, st>>>(p.L0, p.ns, p.npairs0, p.pair_base, p.pair_off0,
                                                  rc, K, p.nc0, sd);
   if (!p.fp64) {
     struct { double *src; void *dst; size_t n; } cp[] = {
         {ptab, p.ptab, n_ptab}, {phi, p.phi_cs, n_phi}, {tw, p.soft_tw, n_tw},
         {sd, p.soft_d, n_softd}, {rc, p.rcoef, n_rc}, {K, p.seedK, n_K},
-        {dcs, p.dft_cs, n_dcs}};
+        {dcs, p.dft_cs, n_dcs}, {ring, p.ring, n_ring}};
     for (auto &c : cp)
       k_to_float<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c.src, (float *)c.dst, (long)c.n);
   }
