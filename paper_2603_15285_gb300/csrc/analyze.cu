@@ -233,8 +233,9 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   // 2. phi DFT.  Fold the pairs (q, q') = (q, np/2 - q), q = 1..Qf, in place:
   //    row q-1 <- x_q + x_q', row q'-1 <- x_q - x_q' (a self-paired middle row,
   //    odd L, stays); even orders then read (SP+, SM-), odd orders (SP-, SM+).
+  const FastDiv dRp(Rp);
   for (int t = tid; t < (K1 / 2) * Rp; t += NT) {
-    int q = t / Rp + 1, r = t - (q - 1) * Rp, q2 = K1 + 1 - q;
+    int q = dRp.div(t) + 1, r = t - (q - 1) * Rp, q2 = K1 + 1 - q;
     T a = SP[(q - 1) * Rp + r], c = SP[(q2 - 1) * Rp + r];
     SP[(q - 1) * Rp + r] = a + c; SP[(q2 - 1) * Rp + r] = a - c;
     a = SM[(q - 1) * Rp + r]; c = SM[(q2 - 1) * Rp + r];
@@ -290,8 +291,9 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   //    F(j) + F(nt-1-j) (even l+m, kept in row j) and F(j) - F(nt-1-j) (odd,
   //    in row nt-1-j); the middle node of odd nt serves both.
   const int Jh = (nt + 1) / 2;
+  const FastDiv dL1(L + 1), dnh(nt / 2 > 0 ? nt / 2 : 1);
   for (int t = tid; t < Gs * (nt / 2) * (L + 1); t += NT) {
-    int m = t % (L + 1), gj = t / (L + 1), g = gj / (nt / 2), j = gj - g * (nt / 2);
+    int gj = dL1.div(t), m = t - gj * (L + 1), g = dnh.div(gj), j = gj - g * (nt / 2);
     T *fa = F + 2 * ((g * nt + j) * Mp + m), *fb = F + 2 * ((g * nt + nt - 1 - j) * Mp + m);
     T ar = fa[0], ai = fa[1], br = fb[0], bi = fb[1];
     fa[0] = ar + br; fa[1] = ai + bi;
