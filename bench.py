@@ -53,11 +53,8 @@ def parse():
     return ap.parse_args()
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+from paper_2603_15285_gb300.shard import (aggregate_rate, barrier as rank_barrier, dist_env,
+                                          max_over_ranks, shard_start)
 
 
 def workload_config(w, B, ws):
@@ -189,7 +186,7 @@ def main():
     import synth
     w = synth.WORKLOADS[WORKLOAD]
     B = args.batch or w.B
-    d = synth.make_batch(w, B=B, start=rank * B, device="cuda")
+    d = synth.make_batch(w, B=B, start=shard_start(rank, B), device="cuda")
     parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
     prec = m.FP32 if args.precision == "fp32" else m.FP64
     plan = m.plan_for_workload(w, precision=prec)
@@ -243,9 +240,7 @@ def main():
         mark(5)
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rank_barrier(ws)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -265,12 +260,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, ws, device="cuda")
     stage_ms = {s: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, s in enumerate(stages)}
     wk = work.sum(0).cpu().numpy()
@@ -280,7 +270,7 @@ def main():
     fp64_peak = SMS * 2 * 2 * clk * 1e6 / 1e12
     achieved = newton_flops / (stage_ms["newton"] * 1e-3) / 1e12
     peak = fp32_peak if prec == m.FP32 else fp64_peak
-    value = ws * B / (ms * 1e-3)
+    value = aggregate_rate(ws, B, ms * 1e-3)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -341,12 +331,8 @@ def main():
         for _ in range(ke):
             m.matcha_align_host(plan, hp, ht, ws=hws, out=hout)
         te = (time.perf_counter() - t0) / ke
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        res["e2e"] = {"value": ws * B / te, "unit": UNIT,
+        te = max_over_ranks(te, ws, device="cuda")
+        res["e2e"] = {"value": aggregate_rate(ws, B, te), "unit": UNIT,
                       "h2d_bytes_per_step": int(hp.numel() * 4 + ht.numel() * 4),
                       "d2h_bytes_per_step": int(B * (13 * 8 + 2 * 4)),
                       "api": "matcha_align_host (pinned host buffers, copies inside the call)"}
