@@ -79,6 +79,9 @@ WORKLOADS = {
     "batch64": Workload("batch64", B=1024, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                         snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
                         L0=8, K=2, P=16, M_iter=3, base_seed=20260317),
+    "deep64": Workload("deep64", B=2048, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
+                       snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32, 40, 48),
+                       L0=8, K=2, P=16, M_iter=3, base_seed=20260319),
     "grad64": Workload("grad64", B=512, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                        snr=0.2, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
                        L0=8, K=2, P=16, M_iter=3, base_seed=20260320, shared_template=True),
