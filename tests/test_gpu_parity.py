@@ -251,3 +251,32 @@ def test_host_buffers_in_several_chunks_match_device_path():
     host = m.matcha_align_host(plan, hp, ht)
     assert np.array_equal(host["R"], dev["R"].cpu().numpy())
     assert np.array_equal(host["best_p"], dev["best_p"].cpu().numpy())
+
+
+def test_align_replays_in_a_cuda_graph():
+    """matcha_align is stream-ordered and allocates nothing, so it can be captured
+    into a CUDA graph; replays give the eager results bit for bit."""
+    w = synth.WORKLOADS["batch64"]
+    B = 8
+    d = synth.make_batch(w, B=B, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    plan = m.plan_for_workload(w, precision=m.FP32)
+    ws = m.alloc_workspace(plan, B)
+    eager = {k: v.clone() for k, v in m.matcha_align(plan, parts, temps, ws=ws).items()}
+    out = {k: torch.empty_like(v) for k, v in eager.items()}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        m.matcha_align(plan, parts, temps, ws=ws, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        m.matcha_align(plan, parts, temps, ws=ws, out=out)
+    for rep in range(2):
+        for v in out.values():
+            v.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for k in eager:
+            assert torch.equal(out[k], eager[k]), (rep, k)
