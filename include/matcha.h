@@ -210,7 +210,10 @@ matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per_dev,
 /* The whole path (a1..a7) for B pairs: particles_dev B volumes, templates_dev
  * volume b * template_batch_stride (0 or 1).  Outputs euler [B][3], R [B][9],
  * score [B], best_p [B], flags [B].  ws_dev must hold
- * matcha_workspace_size(plan, B) bytes (256-byte aligned). */
+ * matcha_workspace_size(plan, B) bytes (256-byte aligned).  The call only
+ * enqueues kernels on `stream` (no allocation, no synchronisation), so it can
+ * be captured into a CUDA graph and replayed with the same buffers; the first
+ * call on a plan should be made before capture. */
 matcha_status matcha_align(matcha_plan plan, const float *particles_dev, const float *templates_dev,
                            int B, int template_batch_stride, const int *P_per_dev,
                            double *euler_dev, double *R_dev, double *score_dev, int *best_p_dev,
