@@ -138,6 +138,7 @@ class Plan:
         self.info = info
         self.precision = precision
         self.P = P
+        self.L_sched = tuple(int(L) for L in L_sched)
         self.L_final = int(L_sched[-1])
         self.box_n = box_n
         self.n_shells = n_shells

@@ -30,7 +30,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 import torch
@@ -60,6 +60,9 @@ class Workload:
     M_iter: int
     base_seed: int
     shared_template: bool = False
+    snr_range: Optional[Tuple[float, float]] = None  # per-particle SNR ~ U[lo, hi] (overrides snr)
+    P_range: Optional[Tuple[int, int]] = None        # per-particle candidate count ~ U{lo..hi}
+    seed_offset: int = 0                             # index of particle 0 in the seed sequence
 
     @property
     def r_max(self) -> float:
@@ -82,6 +85,21 @@ WORKLOADS = {
     "deep64": Workload("deep64", B=2048, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                        snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32, 40, 48),
                        L0=8, K=2, P=16, M_iter=3, base_seed=20260319),
+    # A batch mixing box sizes (2048 x 48^3, 1024 x 64^3, 1024 x 96^3 items of one
+    # seed sequence, in that order): per-particle SNR ~ U[0.05, 0.3] and candidate
+    # count ~ U{8..32}, blobs in a ball of radius floor(0.4 N), S = final L shells.
+    "var48": Workload("var48", B=2048, N=48, n_blobs=32, sigma=2.0, ball_radius=19.0,
+                      snr=None, wedge_deg=60.0, n_shells=24, L_sched=(8, 16, 24),
+                      L0=8, K=2, P=32, M_iter=3, base_seed=20260318, snr_range=(0.05, 0.3),
+                      P_range=(8, 32), seed_offset=0),
+    "var64": Workload("var64", B=1024, N=64, n_blobs=48, sigma=2.0, ball_radius=25.0,
+                      snr=None, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
+                      L0=8, K=2, P=32, M_iter=3, base_seed=20260318, snr_range=(0.05, 0.3),
+                      P_range=(8, 32), seed_offset=2048),
+    "var96": Workload("var96", B=1024, N=96, n_blobs=96, sigma=2.0, ball_radius=38.0,
+                      snr=None, wedge_deg=60.0, n_shells=48, L_sched=(8, 16, 24, 32, 40, 48),
+                      L0=8, K=2, P=32, M_iter=3, base_seed=20260318, snr_range=(0.05, 0.3),
+                      P_range=(8, 32), seed_offset=3072),
     "grad64": Workload("grad64", B=512, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                        snr=0.2, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
                        L0=8, K=2, P=16, M_iter=3, base_seed=20260320, shared_template=True),
@@ -188,11 +206,14 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
     host; rendering runs in chunks of ``chunk`` particles on ``device``.
     """
     B = w.B if B is None else B
-    seeds = np.random.SeedSequence(w.base_seed).spawn(start + B)[start:]
+    first = w.seed_offset + start
+    seeds = np.random.SeedSequence(w.base_seed).spawn(first + B)[first:]
     N = w.N
     parts = torch.empty((B, N, N, N), dtype=torch.float32, device=device)
     temps = None if w.shared_template else torch.empty((B, N, N, N), dtype=torch.float32, device=device)
     Rs = np.empty((B, 3, 3))
+    snrs = np.full(B, w.snr if w.snr is not None else 0.0)
+    P_per = np.full(B, w.P, dtype=np.int32)
     shared = None
     if w.shared_template:
         trng = np.random.default_rng(np.random.SeedSequence(w.base_seed + 7919))
@@ -210,7 +231,11 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
                 offs, amps = shared[0], shared[1]
             offs_l.append(offs); amps_l.append(amps)
             Rs[b] = haar_rotation(rng)
-            if noise and w.snr is not None and w.snr > 0:
+            if w.snr_range is not None:
+                snrs[b] = rng.uniform(*w.snr_range)
+            if w.P_range is not None:
+                P_per[b] = rng.integers(w.P_range[0], w.P_range[1] + 1)
+            if noise and snrs[b] > 0:
                 etas.append(rng.standard_normal((N, N, N), dtype=np.float32))
         Rc = Rs[c0:c0 + len(idx)]
         if shared is None:
@@ -224,7 +249,8 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
         else:
             s = rotate_trilinear(h.contiguous(), Rc)
         if etas:
-            var = (s * s).mean(dim=(1, 2, 3)) / w.snr
+            snr = torch.as_tensor(snrs[c0:c0 + len(idx)], dtype=s.dtype, device=device)
+            var = (s * s).mean(dim=(1, 2, 3)) / snr
             eta = torch.from_numpy(np.stack(etas)).to(device=device, dtype=s.dtype)
             s = s + var.sqrt()[:, None, None, None] * eta
         if w.wedge_deg is not None:
@@ -234,4 +260,6 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
         "templates": temps,
         "particles": parts,
         "R_true": Rs,
+        "snr": snrs,
+        "P_per": P_per,
     }

@@ -1,0 +1,81 @@
+"""A batch mixing box sizes: 48^3 (24 shells, L 8->24), 64^3 (32 shells,
+L 8->32) and 96^3 (48 shells, L 8->48), per-particle SNR and candidate counts
+P_b in 8..32 (P_max = 32).  FP64 results against the oracle (with the
+particle's P_b) on a sample, FP32 results against FP64 within 0.05 degrees,
+and the concurrent group launcher against one call per group."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2603_15285_gb300 as m
+import synth
+from paper_2603_15285_gb300 import mixed
+
+pytestmark = pytest.mark.gpu
+SIZES = {"var48": 48, "var64": 24, "var96": 16}
+
+
+@pytest.fixture(scope="module")
+def groups():
+    import __graft_entry__
+    __graft_entry__.build()
+    out = {}
+    for name, B in SIZES.items():
+        w = synth.WORKLOADS[name]
+        d = synth.make_batch(w, B=B, device="cuda")
+        out[name] = dict(w=w, particles=d["particles"].contiguous(),
+                         templates=d["templates"].contiguous(),
+                         P_per=torch.from_numpy(d["P_per"]).to("cuda"))
+    return out
+
+
+def _align(g, precision):
+    plan = m.plan_for_workload(g["w"], precision=precision)
+    out = m.matcha_align(plan, g["particles"], g["templates"], P_per=g["P_per"])
+    torch.cuda.synchronize()
+    return plan, {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("name", ["var48", "var96"])
+def test_mixed_fp64_matches_oracle(groups, name):
+    g = groups[name]
+    w = g["w"]
+    _, out = _align(g, m.FP64)
+    b = 0
+    Pb = int(g["P_per"][b])
+    ref = O.align_batch(g["particles"][b:b + 1].cpu().numpy(), g["templates"][b:b + 1].cpu().numpy(),
+                        S=w.n_shells, r_max=w.r_max, L0=w.L0, K=w.K, P=Pb, M_iter=w.M_iter,
+                        L_sched=w.L_sched)
+    assert O.rotation_angle(out["R"][b], ref["R"][0]) < 1e-8
+    assert abs(out["score"][b] - ref["score"][0]) <= 1e-10 * abs(ref["score"][0])
+
+
+@pytest.mark.parametrize("name", list(SIZES))
+def test_mixed_fp32_within_005_degrees(groups, name):
+    g = groups[name]
+    _, o64 = _align(g, m.FP64)
+    _, o32 = _align(g, m.FP32)
+    errs = [O.rotation_angle(o32["R"][b], o64["R"][b]) for b in range(SIZES[name])]
+    print("%s fp32 vs fp64: max %.3e deg" % (name, math.degrees(max(errs))))
+    assert math.degrees(max(errs)) < 0.05
+    # fewer candidates than P_b are flagged (bit 3), never more kept than P_b
+    assert np.all(o32["best_p"] < g["P_per"].cpu().numpy())
+
+
+def test_group_launcher_matches_one_call_per_group(groups):
+    plans = {n: m.plan_for_workload(g["w"], precision=m.FP32) for n, g in groups.items()}
+    single = {}
+    for n, g in groups.items():
+        out = m.matcha_align(plans[n], g["particles"], g["templates"], P_per=g["P_per"])
+        single[n] = {k: v.clone() for k, v in out.items()}
+    names = list(groups)
+    res = mixed.align_groups([dict(plan=plans[n], particles=groups[n]["particles"],
+                                   templates=groups[n]["templates"], P_per=groups[n]["P_per"])
+                              for n in names])
+    torch.cuda.synchronize()
+    for n, r in zip(names, res):
+        for k in single[n]:
+            assert torch.equal(r[k], single[n][k]), (n, k)
