@@ -307,3 +307,73 @@ def align_batch(particles, templates, *, S, r_max, L0, K, P, M_iter, L_sched,
                           _d(out["cand_euler"]), _d(out["cand_score"]), _i(out["n_cand"]),
                           ctypes.c_int(n_threads))
     return out
+
+
+# ---- align from SH coefficients ---------------------------------------------
+def align_coefs_batch(f, h, *, S, r_max, L0, K, P, M_iter, L_sched, N=0, n_threads=0,
+                      step_tol=1e-9, accept_tol=1e-11):
+    """Algorithm 1 after the analysis: ``f`` complex [B][S][lm], ``h`` complex
+    [S][lm] (one shared template) or [B][S][lm]."""
+    fa = _split(np.asarray(f))
+    hh = np.asarray(h)
+    ha = _split(hh)
+    B = np.asarray(f).shape[0]
+    per = 2 * S * lm_size(L_sched[-1])
+    hstride = 0 if hh.ndim == 2 else per
+    p = make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol, accept_tol)
+    euler = np.zeros((B, 3)); score = np.zeros(B)
+    best = np.zeros(B, dtype=np.int32); flags = np.zeros(B, dtype=np.int32)
+    lib().orc_align_coefs_batch(ctypes.byref(p), _d(fa), _d(ha), ctypes.c_long(hstride),
+                                ctypes.c_int(B), _d(euler), _d(score), _i(best), _i(flags),
+                                ctypes.c_int(n_threads))
+    return dict(euler=euler, score=score, best_p=best, flags=flags)
+
+
+# ---- template gradient of the refined score ----------------------------------
+def implicit_shift(grad, H):
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    Hm = np.ascontiguousarray(H, dtype=np.float64).reshape(9)
+    v = np.zeros(3)
+    fl = lib().orc_implicit_shift(_d(g), _d(Hm), _d(v))
+    return v, fl
+
+
+def coef_grad(f, S, R, L, abg, v=None, wt=1.0):
+    """dLambda/dh_ln(r_s) (complex [S][lm]) of one particle at rotation abg,
+    with implicit shift v (None: the partial derivative at fixed abg)."""
+    fa = _split(np.asarray(f))
+    a = np.ascontiguousarray(abg, dtype=np.float64)
+    vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    G = np.zeros(2 * S * lm_size(L))
+    lib().orc_coef_grad(_d(fa), ctypes.c_int(S), ctypes.c_double(R), ctypes.c_int(L), _d(a),
+                        _d(vv) if vv is not None else None, ctypes.c_double(wt), _d(G))
+    return (G[0::2] + 1j * G[1::2]).reshape(S, lm_size(L))
+
+
+def analysis_adjoint(G, N, S, R, L):
+    """Transpose of ``analyze_volume`` applied to G (complex [S][lm]); [N][N][N]."""
+    Ga = _split(np.asarray(G))
+    vox = np.zeros(N ** 3)
+    lib().orc_analysis_adjoint(_d(Ga), ctypes.c_int(N), ctypes.c_int(S), ctypes.c_double(R),
+                               ctypes.c_int(L), _d(vox))
+    return vox.reshape(N, N, N)
+
+
+def template_grad_batch(f, h, euler, *, S, r_max, L_sched, wt=None, N=0, n_threads=0):
+    """Per-particle dLambda_b/dh (complex [B][S][lm]) at the refined rotations
+    ``euler`` [B][3]; also returns (v, C) [B][4] and the singular-Hessian flags."""
+    fa = _split(np.asarray(f))
+    hh = np.asarray(h)
+    ha = _split(hh)
+    B = np.asarray(f).shape[0]
+    L = L_sched[-1]
+    per = 2 * S * lm_size(L)
+    hstride = 0 if hh.ndim == 2 else per
+    p = make_params(N, S, r_max, 0, 0, 0, 0, L_sched)
+    e = np.ascontiguousarray(euler, dtype=np.float64)
+    w = None if wt is None else np.ascontiguousarray(wt, dtype=np.float64)
+    G = np.zeros(B * per); out4 = np.zeros((B, 4)); flags = np.zeros(B, dtype=np.int32)
+    lib().orc_template_grad_batch(ctypes.byref(p), _d(fa), _d(ha), ctypes.c_long(hstride),
+                                  ctypes.c_int(B), _d(e), _d(w) if w is not None else None,
+                                  _d(G), _d(out4), _i(flags), ctypes.c_int(n_threads))
+    return (G[0::2] + 1j * G[1::2]).reshape(B, S, lm_size(L)), out4, flags

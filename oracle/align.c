@@ -26,14 +26,13 @@ int orc_max_threads(void) {
 #endif
 }
 
-int orc_align_one(const orc_params *p, const float *particle, const float *tmpl, int P_this,
-                  double *euler, double *R, double *score, int *best_p, int *flags,
-                  int *cand_idx, double *cand_euler0, double *cand_euler,
-                  double *cand_score, int *n_cand) {
+/* Algorithm 1 from the SH coefficients of the particle (f) and the template
+ * (h), complex [S][lm] at L_J: everything after the analysis. */
+int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, int P_this,
+                        double *euler, double *R, double *score, int *best_p, int *flags,
+                        int *cand_idx, double *cand_euler0, double *cand_euler,
+                        double *cand_score, int *n_cand) {
   int LJ = p->L_sched[p->n_levels - 1];
-  int nlm = orc_lm_size(LJ);
-  double *f = (double *)malloc(sizeof(double) * 2 * (size_t)p->S * nlm);
-  double *h = (double *)malloc(sizeof(double) * 2 * (size_t)p->S * nlm);
   double *c = (double *)malloc(sizeof(double) * 2 * (size_t)orc_c_size(LJ));
   int n = orc_soft_n(p->L0, p->K);
   double *grid = (double *)malloc(sizeof(double) * (size_t)n * n * n);
@@ -41,8 +40,6 @@ int orc_align_one(const orc_params *p, const float *particle, const float *tmpl,
   int idx[P > 0 ? P : 1];
   double sc[P > 0 ? P : 1];
 
-  orc_analyze_volume(particle, p->N, p->S, p->r_max, LJ, f);
-  orc_analyze_volume(tmpl, p->N, p->S, p->r_max, LJ, h);
   orc_correlate(f, h, p->S, p->r_max, LJ, c);
   orc_soft_grid(c, p->L0, p->K, grid);
   int nc = orc_local_maxima_topk(grid, n, P, idx, sc);
@@ -80,7 +77,43 @@ int orc_align_one(const orc_params *p, const float *particle, const float *tmpl,
   *best_p = best;
   *flags = fl;
   if (n_cand) *n_cand = nc;
-  free(f); free(h); free(c); free(grid);
+  free(c); free(grid);
+  return 0;
+}
+
+int orc_align_one(const orc_params *p, const float *particle, const float *tmpl, int P_this,
+                  double *euler, double *R, double *score, int *best_p, int *flags,
+                  int *cand_idx, double *cand_euler0, double *cand_euler,
+                  double *cand_score, int *n_cand) {
+  int LJ = p->L_sched[p->n_levels - 1];
+  int nlm = orc_lm_size(LJ);
+  double *f = (double *)malloc(sizeof(double) * 2 * (size_t)p->S * nlm);
+  double *h = (double *)malloc(sizeof(double) * 2 * (size_t)p->S * nlm);
+  orc_analyze_volume(particle, p->N, p->S, p->r_max, LJ, f);
+  orc_analyze_volume(tmpl, p->N, p->S, p->r_max, LJ, h);
+  int rc = orc_align_coefs_one(p, f, h, P_this, euler, R, score, best_p, flags, cand_idx,
+                               cand_euler0, cand_euler, cand_score, n_cand);
+  free(f); free(h);
+  return rc;
+}
+
+/* Batch form of orc_align_coefs_one: f complex [B][S][lm]; h one template
+ * (h_stride = 0) or one per particle (h_stride in doubles). */
+int orc_align_coefs_batch(const orc_params *p, const double *f, const double *h, long h_stride,
+                          int B, double *euler, double *score, int *best_p, int *flags,
+                          int n_threads) {
+  int LJ = p->L_sched[p->n_levels - 1];
+  long per = 2L * p->S * orc_lm_size(LJ);
+#ifdef _OPENMP
+  if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+  for (int b = 0; b < B; ++b) {
+    double R[9];
+    orc_align_coefs_one(p, f + b * per, h + b * h_stride, p->P, euler + 3 * b, R, score + b,
+                        best_p + b, flags + b, NULL, NULL, NULL, NULL, NULL);
+  }
+  (void)n_threads;
   return 0;
 }
 

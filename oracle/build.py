@@ -9,7 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["quadrature.c", "sampling.c", "sh_analysis.c", "contraction.c", "wigner.c",
-           "objective.c", "soft.c", "newton.c", "align.c"]
+           "objective.c", "soft.c", "newton.c", "align.c", "adjoint.c"]
 OUT = os.path.join(HERE, "_build", "liboracle.so")
 
 

@@ -98,7 +98,25 @@ int orc_align_batch(const orc_params *p, const float *particles, const float *te
                     double *euler, double *R, double *score, int *best_p, int *flags,
                     int *cand_idx, double *cand_euler0, double *cand_euler,
                     double *cand_score, int *n_cand, int n_threads);
+int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, int P_this,
+                        double *euler, double *R, double *score, int *best_p, int *flags,
+                        int *cand_idx, double *cand_euler0, double *cand_euler,
+                        double *cand_score, int *n_cand);
+int orc_align_coefs_batch(const orc_params *p, const double *f, const double *h, long h_stride,
+                          int B, double *euler, double *score, int *best_p, int *flags,
+                          int n_threads);
 int orc_max_threads(void);
+
+/* ---- template gradient of the refined score (adjoint.c) ---------------- */
+int  orc_implicit_shift(const double *grad, const double *H, double *v);
+void orc_coef_grad(const double *f, int S, double R, int L, const double *abg, const double *v,
+                   double wt, double *G);
+void orc_analysis_adjoint(const double *G, int N, int S, double R, int L, double *vox);
+int  orc_template_grad_one(const orc_params *p, const double *f, const double *h,
+                           const double *abg, double wt, double *G, double *out4);
+int  orc_template_grad_batch(const orc_params *p, const double *f, const double *h, long h_stride,
+                             int B, const double *euler, const double *wt, double *G,
+                             double *out4, int *flags, int n_threads);
 
 #ifdef __cplusplus
 }
