@@ -233,6 +233,50 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
                                 double *score, int *best_p, int *flags, void *ws_dev,
                                 size_t ws_bytes, void *stream);
 
+/* Gradient of the refined scores with respect to the template.
+ *
+ * Loss Lambda = sum_b w_b C_{L_J}(theta*_b), theta*_b the refined rotation of
+ * particle b (Algorithm 1).  The template h enters C through
+ * c^l_{mn} = sum_s w_s f_lm(r_s) conj(h_ln(r_s)) (Eq. sigmalmm, Appendix A.5),
+ * and theta* moves with h so that grad C stays zero (Section 2.2); by the
+ * implicit function theorem
+ *   dLambda_b/dh = dC/dh - (grad C)^T H^{-1} d(grad C)/dh   at theta*_b,
+ * the second term through the analytic Hessian H.  Wigner d and its
+ * derivative are recomputed by the l-recurrence; nothing is kept from the
+ * forward pass but its outputs.
+ *
+ * Inputs (device, plan precision unless stated):
+ *   f_dev      particles' SH coefficients [B][S][n_lm][2] (matcha_analyze);
+ *   c_dev      correlation coefficients [B][corr_entries][4]
+ *              (matcha_correlate_coeffs with the same template);
+ *   euler_dev  double [B][3]: the refined rotations (matcha_final_select);
+ *   weight_dev double [B]: w_b (the upstream gradient), NULL = all ones;
+ *   template_batch_stride 0: one template shared by all particles (the
+ *              gradients are summed over b); 1: one template per particle.
+ * Outputs (device; n_t = 1 for a shared template, B otherwise):
+ *   coef_grad_dev  [n_t][S][n_lm][2], plan precision: dLambda/dRe h_ln(r_s)
+ *              and dLambda/dIm h_ln(r_s) of the stored coefficients
+ *              (0 <= n <= l), each collecting the terms of its mirror
+ *              h_{l,-n} = (-1)^n conj(h_ln);
+ *   vox_grad_dev   double [n_t][N][N][N] (C order [z][y][x]): dLambda/dvoxel
+ *              through the shell analysis and trilinear sampling; NULL skips
+ *              it.  Overwritten (zeroed first); sums by atomic adds, so the
+ *              last bits may vary between runs;
+ *   shift_dev  double [B][4] or NULL: (v, C) with v = H^{-1} grad C at theta*
+ *              and C = C_{L_J}(theta*);
+ *   flags_dev  int [B] or NULL: 16 when H is singular at theta* (no isolated
+ *              maximum; the implicit term is dropped for that particle), else 0.
+ * ws_dev: matcha_template_grad_workspace_size bytes, 256-byte aligned.
+ * Asynchronous on `stream`.  MATCHA_ERR_UNSUPPORTED when the per-degree
+ * tables do not fit in shared memory (FP64 above L_J = 58). */
+matcha_status matcha_template_grad_workspace_size(matcha_plan plan, int B,
+                                                  int template_batch_stride, size_t *bytes);
+matcha_status matcha_template_grad(matcha_plan plan, const void *f_dev, const void *c_dev, int B,
+                                   int template_batch_stride, const double *euler_dev,
+                                   const double *weight_dev, void *coef_grad_dev,
+                                   double *vox_grad_dev, double *shift_dev, int *flags_dev,
+                                   void *ws_dev, size_t ws_bytes, void *stream);
+
 const char *matcha_status_string(matcha_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char *matcha_last_error(void);

@@ -28,7 +28,7 @@ SYMBOLS = [
     "matcha_workspace_size", "matcha_analyze", "matcha_correlate_coeffs", "matcha_soft_search",
     "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
-    "matcha_soft_search_noalloc",
+    "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
 ]
 
 
@@ -77,6 +77,8 @@ def lib():
             "matcha_align": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_host_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
             "matcha_align_host": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
+            "matcha_template_grad_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
+            "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -335,6 +337,49 @@ def matcha_align_host(plan: Plan, particles: np.ndarray, templates: np.ndarray, 
                                    hp(out["best_p"]), hp(out["flags"]), aligned, nbytes, _stream()),
            "matcha_align_host")
     return out
+
+
+def align_from_coefs(plan: Plan, f, h, h_batch_stride: int, P_per=None):
+    """Steps a3..a7 from SH coefficients (``matcha_analyze`` layout): the
+    contraction, the SOFFT search, the Newton march and the final selection.
+    Returns the final selection plus ``c`` (the correlation coefficients)."""
+    c = matcha_correlate_coeffs(plan, f, h, h_batch_stride)
+    soft = matcha_soft_search(plan, c, P_per=P_per)
+    nm = matcha_newton_march(plan, c, soft["n_cand"], soft["euler"])
+    out = matcha_final_select(plan, soft["n_cand"], nm["euler"], nm["score"], nm["flags"], P_per=P_per)
+    out["c"] = c
+    return out
+
+
+def matcha_template_grad(plan: Plan, f, c, euler, weight=None, template_batch_stride: int = 0,
+                         voxels: bool = True):
+    """Gradient of sum_b weight_b C_{L_J}(theta*_b) with respect to the
+    template: ``coef_grad`` [n_t][S][n_lm][2] (plan precision) and
+    ``vox_grad`` [n_t][N][N][N] (float64), n_t = 1 for a shared template;
+    also ``shift`` [B][4] = (H^{-1} grad C, C) and ``flags`` [B]."""
+    torch = _torch()
+    _need(f, plan.real_dtype, "f"); _need(c, plan.real_dtype, "c")
+    _need(euler, torch.float64, "euler")
+    if weight is not None:
+        _need(weight, torch.float64, "weight")
+    B = f.shape[0]
+    nt = B if template_batch_stride else 1
+    N = plan.box_n
+    coef_grad = torch.empty((nt, plan.n_shells, plan.info.n_lm, 2), dtype=plan.real_dtype, device="cuda")
+    vox_grad = torch.empty((nt, N, N, N), dtype=torch.float64, device="cuda") if voxels else None
+    shift = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+    flags = torch.empty((B,), dtype=torch.int32, device="cuda")
+    need = ctypes.c_size_t(0)
+    _check(lib().matcha_template_grad_workspace_size(plan.handle, B, template_batch_stride,
+                                                     ctypes.byref(need)), "matcha_template_grad")
+    ws = torch.empty((need.value + 256,), dtype=torch.uint8, device="cuda")
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    _check(lib().matcha_template_grad(plan.handle, _ptr(f), _ptr(c), B, template_batch_stride,
+                                      _ptr(euler), _ptr(weight), _ptr(coef_grad), _ptr(vox_grad),
+                                      _ptr(shift), _ptr(flags), aligned, need.value, _stream()),
+           "matcha_template_grad")
+    return dict(coef_grad=coef_grad, vox_grad=vox_grad, shift=shift, flags=flags)
 
 
 def corr_layout(L: int):

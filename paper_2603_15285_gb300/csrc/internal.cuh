@@ -86,6 +86,11 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
 template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st);
+template <typename T>
+cudaError_t launch_template_grad(const Plan &p, const T *f, const T *c, int B, int tstride,
+                                 const double *euler, const double *weight, T *X, T *coef_grad,
+                                 double *vox_grad, double *shift, int *flags, cudaStream_t st);
+bool backward_fits(const Plan &p);  // the template-gradient kernel's shared memory fits
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
 cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,

@@ -408,4 +408,53 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
   return MATCHA_OK;
 }
 
+// Template gradient of the refined scores: workspace = per-particle shifts
+// (v, C) and, for a shared template, the per-particle coefficient gradients
+// before their sum.
+static size_t grad_ws(const Plan &p, int B, int tstride, double **shift, void **X, char *base) {
+  Carve cv{base};
+  *shift = cv.take<double>(4 * (size_t)B);
+  *X = tstride ? nullptr : cv.take<char>(real_size(p) * 2 * (size_t)p.S * p.nlm * B);
+  return cv.off;
+}
+
+matcha_status matcha_template_grad_workspace_size(matcha_plan plan, int B, int tstride,
+                                                  size_t *bytes) {
+  if (!plan || !bytes || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  double *sh;
+  void *X;
+  *bytes = grad_ws(*P_(plan), B, tstride, &sh, &X, nullptr);
+  return MATCHA_OK;
+}
+
+matcha_status matcha_template_grad(matcha_plan plan, const void *f, const void *c, int B,
+                                   int tstride, const double *euler, const double *weight,
+                                   void *coef_grad, double *vox_grad, double *shift_out,
+                                   int *flags, void *ws, size_t ws_bytes, void *stream) {
+  if (!plan || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  if (B == 0) return MATCHA_OK;
+  if (!f || !c || !euler || !coef_grad || !ws) return MATCHA_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  if (!backward_fits(*p)) {
+    set_error_text("template gradient: the per-degree tables of this bandwidth exceed shared memory");
+    return MATCHA_ERR_UNSUPPORTED;
+  }
+  double *shift;
+  void *X;
+  if (ws_bytes < grad_ws(*p, B, tstride, &shift, &X, nullptr)) return MATCHA_ERR_WORKSPACE;
+  grad_ws(*p, B, tstride, &shift, &X, (char *)ws);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e =
+      p->fp64 ? launch_template_grad<double>(*p, (const double *)f, (const double *)c, B, tstride,
+                                             euler, weight, (double *)X, (double *)coef_grad,
+                                             vox_grad, shift, flags, st)
+              : launch_template_grad<float>(*p, (const float *)f, (const float *)c, B, tstride,
+                                            euler, weight, (float *)X, (float *)coef_grad,
+                                            vox_grad, shift, flags, st);
+  if (e != cudaSuccess) return fail_cuda(e, "template_grad");
+  if (shift_out) CK(cudaMemcpyAsync(shift_out, shift, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
+  return MATCHA_OK;
+}
+
 }  // extern "C"
