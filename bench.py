@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
     return ap.parse_args()
 
@@ -136,6 +137,44 @@ def newton_traffic(B):
     if hashlib.sha256(src).hexdigest() != meta.get("sha256"):
         return None
     return meta["dram_bytes_per_launch_1024"] * B / 1024.0
+
+
+def time_backward(st, reps=5):
+    """Template gradient of the refined scores on the shared-template 64^3
+    workload (512 particles, L 8 -> 32): forward (a1..a7 from the template's
+    and particles' analyses) and matcha_template_grad timed apart, FP32 and
+    FP64 plans; the gradient itself is checked against the oracle's adjoint
+    and central differences in the tests."""
+    import torch
+    import paper_2603_15285_gb300 as m
+    import synth
+    wg = synth.WORKLOADS["grad64"]
+    d = synth.make_batch(wg, device="cuda")
+    parts, temp = d["particles"], d["templates"]
+    out = {"workload": "grad64: %d particles, one shared %d^3 template, S=%d, L %s, P=%d"
+                       % (wg.B, wg.N, wg.n_shells, "->".join(map(str, wg.L_sched)), wg.P)}
+    for name, prec in (("fp32", m.FP32), ("fp64", m.FP64)):
+        plan = m.plan_for_workload(wg, precision=prec)
+        f = m.matcha_analyze(plan, parts)
+        h = m.matcha_analyze(plan, temp)
+        fw = m.align_from_coefs(plan, f, h, 0)
+        m.matcha_template_grad(plan, f, fw["c"], fw["euler"])
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(st)
+        for _ in range(reps):
+            fw = m.align_from_coefs(plan, f, h, 0)
+        e[1].record(st)
+        for _ in range(reps):
+            g = m.matcha_template_grad(plan, f, fw["c"], fw["euler"])
+        e[2].record(st)
+        torch.cuda.synchronize()
+        fms, bms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        out[name] = {"forward_ms": fms, "backward_ms": bms,
+                     "backward_particles_per_s": wg.B / (bms * 1e-3),
+                     "singular_hessians": int((g["flags"] != 0).sum().item())}
+        plan.close()
+    return out
 
 
 def run_reference(args):
@@ -349,6 +388,8 @@ def main():
                            "particles_over_0.05deg": int((errs > 0.05).sum()),
                            "note": "FP64 GPU path matches the FP64 oracle to 1e-8 rad (tests)"}
         del ws64
+    if rank == 0 and not args.no_backward:
+        res["backward"] = time_backward(st)
     if not args.no_e2e:
         hp = torch.empty_like(parts, device="cpu").pin_memory()
         hp.copy_(parts)
