@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="matcha", choices=["matcha", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -227,7 +227,9 @@ def main():
     B = args.batch or w.B
     d = synth.make_batch(w, B=B, start=shard_start(rank, B), device="cuda")
     parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
-    prec = m.FP32 if args.precision == "fp32" else m.FP64
+    PRECS = {"fp32": m.FP32, "fp64": m.FP64, "tf32": m.TF32, "bf16": m.BF16}
+    prec = PRECS[args.precision]
+    is32 = prec != m.FP64
     plan = m.plan_for_workload(w, precision=prec)
     n = plan.info.soft_n
     rt = plan.real_dtype
@@ -344,28 +346,31 @@ def main():
     fp32_peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12  # TFLOP/s
     fp64_peak = SMS * 2 * 2 * clk * 1e6 / 1e12
     achieved = newton_flops / (stage_ms["newton"] * 1e-3) / 1e12
-    peak = fp32_peak if prec == m.FP32 else fp64_peak
+    peak = fp32_peak if is32 else fp64_peak
     value = aggregate_rate(ws, B, ms * 1e-3)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == m.FP32 else "f64",
+        "vs_baseline": None, "dtype": "f32" if is32 else "f64",
+        "contraction": {m.FP32: "FP32 CUDA cores", m.FP64: "FP64 CUDA cores",
+                        m.TF32: "tcgen05 TF32 operands, FP32 accumulation",
+                        m.BF16: "tcgen05 BF16 operands, FP32 accumulation"}[prec],
         "data": "synthetic (seeded Gaussian-blob volumes; no dataset)",
         "config": workload_config(w, B, ws),
         "timed": timed_how,
         "stage_ms": stage_ms,
         "roofline": {"kernel": "k_newton", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": newton_traffic(B) if prec == m.FP32 else None,
+                     "traffic": newton_traffic(B) if is32 else None,
                      "peak_source": "%d SMs x %d %s lanes x 2 x %.0f MHz (max SM clock seen)"
-                                    % (SMS, FP32_LANES if prec == m.FP32 else 2,
-                                       "FP32" if prec == m.FP32 else "FP64", clk),
+                                    % (SMS, FP32_LANES if is32 else 2,
+                                       "FP32" if is32 else "FP64", clk),
                      "flops_per_launch": newton_flops},
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
     }
     # accuracy of the timed path against the FP64 GPU path (oracle-checked in the tests)
-    if rank == 0 and not args.no_fp64 and prec == m.FP32:
+    if rank == 0 and not args.no_fp64 and is32:
         plan64 = m.plan_for_workload(w, precision=m.FP64)
         ws64 = m.alloc_workspace(plan64, B)
         o64 = m.matcha_align(plan64, parts, temps, ws=ws64)
@@ -388,6 +393,29 @@ def main():
                            "particles_over_0.05deg": int((errs > 0.05).sum()),
                            "note": "FP64 GPU path matches the FP64 oracle to 1e-8 rad (tests)"}
         del ws64
+        # the other 32-bit plans (contraction on CUDA cores or tensor cores), eager timing
+        others = {}
+        for name, pr in (("fp32", m.FP32), ("tf32", m.TF32), ("bf16", m.BF16)):
+            if pr == prec:
+                continue
+            po = m.plan_for_workload(w, precision=pr)
+            wso = m.alloc_workspace(po, B)
+            oo = m.matcha_align(po, parts, temps, ws=wso)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(k64 * 5):
+                m.matcha_align(po, parts, temps, ws=wso, out=oo)
+            e1.record(st)
+            torch.cuda.synchronize()
+            mso = e0.elapsed_time(e1) / (k64 * 5)
+            Ro = oo["R"].cpu().numpy()
+            eo = np.degrees([oracle.rotation_angle(Ro[b], R64[b]) for b in range(B)])
+            others[name] = {"value": B / (mso * 1e-3), "unit": UNIT, "ms_per_step": mso,
+                            "timed": "matcha_align, eager", "max_err_deg_vs_fp64_gpu": float(eo.max()),
+                            "p90_err_deg_vs_fp64_gpu": float(np.percentile(eo, 90))}
+            del wso
+            po.close()
+        res["other_32bit_paths"] = others
     if rank == 0 and not args.no_backward:
         res["backward"] = time_backward(st)
     if not args.no_e2e:

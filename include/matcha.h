@@ -17,7 +17,10 @@
  *     allocates or frees in those calls (only plan create/destroy do);
  *   - precision: a plan computes either in FP64 throughout (MATCHA_FP64) or
  *     in FP32 with FP64 angles, acceptance tests and final comparisons (MATCHA_FP32);
- *     "real" below is double for FP64 plans and float for FP32 plans, and a
+ *     MATCHA_TF32 and MATCHA_BF16 are FP32 plans whose per-degree contraction
+ *     (step a3) runs on the tensor cores (tcgen05) with TF32 or BF16 operands and
+ *     FP32 accumulation, for L_J <= 63;
+ *     "real" below is double for FP64 plans and float for the others, and a
  *     complex number is two consecutive reals (re, im);
  *   - volumes: float32, C order [z][y][x], N^3 per volume, voxel [k][j][i] at
  *     position (x, y, z) = (i, j, k), rotation centre c0 = N/2, trilinear
@@ -71,7 +74,7 @@ typedef enum {
   MATCHA_ERR_UNSUPPORTED = 5  /* valid but not implemented (e.g. a size limit) */
 } matcha_status;
 
-typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1 } matcha_precision;
+typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1, MATCHA_TF32 = 2, MATCHA_BF16 = 3 } matcha_precision;
 
 /* Plan descriptor: the parameters of Algorithm 1 plus the sampling of the ball.
  *   box_n        N, volume edge (4 .. 512)
@@ -126,6 +129,11 @@ matcha_status matcha_plan_create(const matcha_plan_desc *desc, matcha_plan *out)
 /* Frees the plan's tables; NULL is accepted. Synchronises the device. */
 matcha_status matcha_plan_destroy(matcha_plan plan);
 matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info);
+/* Reads (synchronously) the plan's device status word: bit 0 is set when a
+ * tensor-core kernel's wait for its MMAs reached its iteration limit (its
+ * output block is then left unwritten).  Returns MATCHA_ERR_TIMEOUT when any
+ * bit is set, else MATCHA_OK. */
+matcha_status matcha_plan_device_status(matcha_plan plan, int *bits);
 
 /* Copies one of the plan's FP64 quadrature tables to the host (synchronous):
  * which = 0 radial nodes r_s, 1 radial weights w_s (r^2 Jacobian included),

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmatcha.so")
 MATCHA_MAX_LEVELS = 16
 MATCHA_MAX_L = 64
 MATCHA_MAX_P = 32
-FP64, FP32 = 0, 1
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 
 # exported symbols, in include/matcha.h order
 SYMBOLS = [
@@ -29,6 +29,7 @@ SYMBOLS = [
     "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
     "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
+    "matcha_plan_device_status",
 ]
 
 
@@ -78,6 +79,7 @@ def lib():
             "matcha_host_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
             "matcha_align_host": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_template_grad_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
+            "matcha_plan_device_status": [_vp, ctypes.POINTER(i)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
         }
         for name, args in sigs.items():
@@ -172,6 +174,12 @@ class Plan:
         _check(lib().matcha_plan_table(self._h, which, out.ctypes.data, n.value, ctypes.byref(n)),
                "matcha_plan_table")
         return out
+
+    def device_status(self) -> int:
+        """The plan's device status bits (bit 0: a tensor-core wait hit its limit)."""
+        bits = ctypes.c_int(0)
+        lib().matcha_plan_device_status(self.handle, ctypes.byref(bits))
+        return bits.value
 
     def workspace_size(self, B: int) -> int:
         s = ctypes.c_size_t()

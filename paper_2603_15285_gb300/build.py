@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "_lib", "libmatcha.so")
 SOURCES = ["matcha_api.cu", "plan_tables.cu", "analyze.cu", "correlate.cu", "soft.cu", "newton.cu",
-           "noalloc.cu", "backward.cu"]
+           "noalloc.cu", "backward.cu",
+           "correlate_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

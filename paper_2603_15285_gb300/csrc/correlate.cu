@@ -137,6 +137,8 @@ template <typename T>
 cudaError_t launch_correlate(const Plan &p, const T *f, const T *h, int B, int hstride, T *c,
                              cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  if (sizeof(T) == 4 && p.tc)
+    return launch_correlate_tc(p, (const float *)f, (const float *)h, B, hstride, (float *)c, st);
   size_t smem = sizeof(T) * 4 * (size_t)p.S * (p.LJ + 2);  // both degrees of a pair
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {

@@ -14,6 +14,8 @@ struct Plan {
   int Ls[MATCHA_MAX_LEVELS];
   double R, step_tol, accept_tol;
   bool fp64;
+  int tc;        // contraction on the tensor cores: 0 no, 1 TF32, 2 BF16 (FP32 plans)
+  int *dev_err;  // device word: bit 0 = a tensor-core wait reached its limit
   int nt, np, nlm, npairs, npairs0, ns;
   int ngroups;  // partner groups of the correlation layout, (L_J+1)(L_J+2)/2
   long nc;      // pair slots x degrees per particle (dummy halves included), 4 reals each
@@ -90,6 +92,9 @@ template <typename T>
 cudaError_t launch_template_grad(const Plan &p, const T *f, const T *c, int B, int tstride,
                                  const double *euler, const double *weight, T *X, T *coef_grad,
                                  double *vox_grad, double *shift, int *flags, cudaStream_t st);
+cudaError_t launch_correlate_tc(const Plan &p, const float *f, const float *h, int B, int hstride,
+                                float *c, cudaStream_t st);
+bool correlate_tc_fits(int S, int L, int bytes);
 bool backward_fits(const Plan &p);  // the template-gradient kernel's shared memory fits
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid

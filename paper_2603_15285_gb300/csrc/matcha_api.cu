@@ -97,7 +97,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   for (int i = 1; i < d->n_levels; ++i)
     if (d->L_sched[i] <= d->L_sched[i - 1]) return MATCHA_ERR_INVALID_ARG;
   if (d->L_sched[d->n_levels - 1] > MATCHA_MAX_L) return MATCHA_ERR_UNSUPPORTED;
-  if (d->precision != MATCHA_FP64 && d->precision != MATCHA_FP32) return MATCHA_ERR_INVALID_ARG;
+  if (d->precision < MATCHA_FP64 || d->precision > MATCHA_BF16) return MATCHA_ERR_INVALID_ARG;
   if (!isfinite(d->r_max) || !isfinite(d->step_tol) || !isfinite(d->accept_tol))
     return MATCHA_ERR_INVALID_ARG;
 
@@ -109,6 +109,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->LJ = d->L_sched[d->n_levels - 1];
   p->R = d->r_max > 0 ? d->r_max : 0.5 * d->box_n - 1.0;
   p->fp64 = d->precision == MATCHA_FP64;
+  p->tc = d->precision == MATCHA_TF32 ? 1 : d->precision == MATCHA_BF16 ? 2 : 0;
   p->step_tol = d->step_tol > 0 ? d->step_tol : (p->fp64 ? 1e-9 : 1e-6);
   p->accept_tol = d->accept_tol > 0 ? d->accept_tol : (p->fp64 ? 1e-11 : 1e-5);
   p->nt = p->LJ + 1;
@@ -132,6 +133,15 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
     set_error_text(msg);
     return MATCHA_ERR_UNSUPPORTED;
   }
+  if (p->tc && !correlate_tc_fits(p->S, p->LJ, p->tc == 2 ? 2 : 4)) {
+    char msg[160];
+    snprintf(msg, sizeof(msg),
+             "plan: the tensor-core contraction takes L_J <= 63 (4(L_J+1) accumulator columns "
+             "<= 256); L_J = %d", p->LJ);
+    delete p;
+    set_error_text(msg);
+    return MATCHA_ERR_UNSUPPORTED;
+  }
   std::vector<int> base(p->npairs), off0(p->npairs0);
   for (int m = 0; m <= p->LJ; ++m)
     for (int n = -m; n <= m; ++n) {
@@ -148,6 +158,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
   size_t o_dcs = add(rs * 4 * (size_t)p->Qf * p->Mq);
   size_t o_ring = add(rs * 2 * (size_t)p->S * p->nt);
+  size_t o_err = add(sizeof(int));
   cudaError_t e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
   char *b = (char *)p->base;
@@ -158,7 +169,9 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->pair_base = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
   p->dft_cs = b + o_dcs;
   p->ring = b + o_ring;
-  e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
+  p->dev_err = (int *)(b + o_err);
+  e = cudaMemset(p->dev_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = build_tables(*p, 0);
   if (e != cudaSuccess) {
@@ -181,6 +194,13 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
   delete p;
   if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
   return MATCHA_OK;
+}
+
+matcha_status matcha_plan_device_status(matcha_plan plan, int *bits) {
+  if (!plan || !bits) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  CK(cudaMemcpy(bits, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return *bits ? MATCHA_ERR_TIMEOUT : MATCHA_OK;
 }
 
 matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info) {
