@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
     return ap.parse_args()
 
@@ -175,6 +176,43 @@ def time_backward(st, reps=5):
                      "singular_hessians": int((g["flags"] != 0).sum().item())}
         plan.close()
     return out
+
+
+def time_mixed(st, prec, reps=5):
+    """The mixed-size batch (2048 x 48^3 / L 24, 1024 x 64^3 / L 32, 1024 x
+    96^3 / L 48; per-particle SNR and candidate counts): autotuned plans, all
+    groups captured in one CUDA graph (concurrent streams, costliest first)
+    and replayed."""
+    import torch
+    import paper_2603_15285_gb300 as m
+    import synth
+    from paper_2603_15285_gb300 import mixed
+    groups, total = [], 0
+    for name in ("var48", "var64", "var96"):
+        w = synth.WORKLOADS[name]
+        d = synth.make_batch(w, device="cuda")
+        groups.append(dict(plan=m.plan_for_workload(w, precision=prec),
+                           particles=d["particles"].contiguous(),
+                           templates=d["templates"].contiguous(),
+                           P_per=torch.from_numpy(d["P_per"]).to("cuda")))
+        total += w.B
+    mb = mixed.MixedBatch(groups, autotune=True).capture()
+    for _ in range(2):
+        mb.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        mb.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "mixed: 2048 x 48^3 (S 24, L 8..24) + 1024 x 64^3 (S 32, L 8..32) + "
+                        "1024 x 96^3 (S 48, L 8..48), P_b ~ U{8..32}, SNR ~ U[0.05, 0.3]",
+            "particles": total, "ms_per_step": ms, "value": total / (ms * 1e-3),
+            "unit": "particles/s", "timed": "one CUDA graph of all groups, replayed",
+            "autotune": [{"shells_per_analysis_cta": t["analyze_shells"],
+                          "tc_ctas_per_sm": t["tc_ctas_per_sm"]} for t in mb.tune]}
 
 
 def run_reference(args):
@@ -416,8 +454,6 @@ def main():
             del wso
             po.close()
         res["other_32bit_paths"] = others
-    if rank == 0 and not args.no_backward:
-        res["backward"] = time_backward(st)
     if not args.no_e2e:
         hp = torch.empty_like(parts, device="cpu").pin_memory()
         hp.copy_(parts)
@@ -443,6 +479,14 @@ def main():
                       "d2h_bytes_per_step": int(B * (13 * 8 + 2 * 4)),
                       "api": "matcha_align_host (pinned host buffers, copies inside the call)"}
         del hws
+    # further workloads, after the end-to-end measurement so that their device
+    # allocations cannot affect it
+    if rank == 0 and not args.no_backward:
+        res["backward"] = time_backward(st)
+    if rank == 0 and not args.no_mixed:
+        res["mixed"] = time_mixed(st, prec)
+        import torch
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.max_threads()

@@ -241,6 +241,24 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
                                 double *score, int *best_p, int *flags, void *ws_dev,
                                 size_t ws_bytes, void *stream);
 
+/* Autotuning.  Times, on the given batch, the tile choices that leave every
+ * result bit unchanged and keeps the fastest in the plan: the shells per
+ * analysis CTA (1, 2, 4 or 8, those whose shared memory fits) and, for TF32 /
+ * BF16 plans, the tensor-core contraction's CTAs per SM (1 or 2).  Uses the
+ * matcha_align workspace for its scratch; synchronises `stream` (not
+ * graph-capturable: tune first, then capture).  report: the choices and the
+ * best time (ms) of each candidate, -1 where a candidate does not apply. */
+typedef struct {
+  int analyze_shells;
+  float analyze_ms[4];     /* candidates 1, 2, 4, 8 shells per CTA */
+  int tc_ctas_per_sm;      /* 0 when the plan's contraction runs on the CUDA cores */
+  float tc_ms[2];          /* candidates 1, 2 CTAs per SM */
+} matcha_tune_report;
+matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles_dev,
+                                   const float *templates_dev, int B, int template_batch_stride,
+                                   void *ws_dev, size_t ws_bytes, void *stream,
+                                   matcha_tune_report *report);
+
 /* Gradient of the refined scores with respect to the template.
  *
  * Loss Lambda = sum_b w_b C_{L_J}(theta*_b), theta*_b the refined rotation of

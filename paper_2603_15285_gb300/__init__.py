@@ -29,7 +29,7 @@ SYMBOLS = [
     "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
     "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
-    "matcha_plan_device_status",
+    "matcha_plan_device_status", "matcha_plan_autotune",
 ]
 
 
@@ -49,6 +49,11 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n_lm", ctypes.c_int), ("coeff_count", ctypes.c_long),
                 ("corr_entries", ctypes.c_long), ("n_pairs", ctypes.c_int),
                 ("soft_n", ctypes.c_int), ("real_bytes", ctypes.c_int)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("analyze_shells", ctypes.c_int), ("analyze_ms", ctypes.c_float * 4),
+                ("tc_ctas_per_sm", ctypes.c_int), ("tc_ms", ctypes.c_float * 2)]
 
 
 _lib = None
@@ -80,6 +85,7 @@ def lib():
             "matcha_align_host": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_template_grad_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
             "matcha_plan_device_status": [_vp, ctypes.POINTER(i)],
+            "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
         }
         for name, args in sigs.items():
@@ -174,6 +180,24 @@ class Plan:
         _check(lib().matcha_plan_table(self._h, which, out.ctypes.data, n.value, ctypes.byref(n)),
                "matcha_plan_table")
         return out
+
+    def autotune(self, particles, templates, ws=None) -> dict:
+        """Times the result-invariant tile choices on this batch and keeps the
+        fastest in the plan (``matcha_plan_autotune``); returns the report."""
+        torch = _torch()
+        _need(particles, torch.float32, "particles"); _need(templates, torch.float32, "templates")
+        B = particles.shape[0]
+        stride = 0 if templates.shape[0] == 1 and B != 1 else 1
+        if ws is None:
+            ws = alloc_workspace(self, B)
+        base = ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        rep = TuneReport()
+        _check(lib().matcha_plan_autotune(self.handle, _ptr(particles), _ptr(templates), B, stride,
+                                          aligned, ws.numel() - (aligned - base), _stream(),
+                                          ctypes.byref(rep)), "matcha_plan_autotune")
+        return dict(analyze_shells=rep.analyze_shells, analyze_ms=list(rep.analyze_ms),
+                    tc_ctas_per_sm=rep.tc_ctas_per_sm, tc_ms=list(rep.tc_ms))
 
     def device_status(self) -> int:
         """The plan's device status bits (bit 0: a tensor-core wait hit its limit)."""

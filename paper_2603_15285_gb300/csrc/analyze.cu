@@ -339,14 +339,9 @@ template <typename T>
 cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   {
-    // shells per CTA: a divisor of S in {8, 4, 2, 1} whose shared memory fits
-    // (MATCHA_ANALYZE_SHELLS overrides the preferred size, for tuning)
-    static int G_env = -1;
-    if (G_env < 0) {
-      const char *e = getenv("MATCHA_ANALYZE_SHELLS");
-      G_env = e ? atoi(e) : 0;
-    }
-    int G = G_env > 0 ? G_env : 2;
+    // shells per CTA: a divisor of S in {8, 4, 2, 1} whose shared memory fits;
+    // 2 unless the plan was autotuned (matcha_plan_autotune)
+    int G = p.tune_shells > 0 ? p.tune_shells : 2;
     G = G >= 8 ? 8 : G >= 4 ? 4 : G >= 2 ? 2 : 1;
     while (G > 1 && (p.S % G != 0 || analyze2_smem<T>(p, G) > 100 * 1024)) G >>= 1;
     size_t smem = analyze2_smem<T>(p, G);
@@ -370,6 +365,12 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
   k_analyze<T><<<dim3(p.S, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj, (const T *)p.ptab,
                                                  (const T *)p.phi_cs, coef);
   return cudaGetLastError();
+}
+
+bool analyze_shells_ok(const Plan &p, int G) {
+  if (G != 1 && G != 2 && G != 4 && G != 8) return false;
+  if (p.S % G) return false;
+  return p.fp64 ? analyze2_smem<double>(p, G) <= 100 * 1024 : analyze2_smem<float>(p, G) <= 100 * 1024;
 }
 
 template cudaError_t launch_analyze<float>(const Plan &, const float *, int, float *, cudaStream_t);

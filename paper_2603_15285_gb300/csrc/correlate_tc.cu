@@ -376,7 +376,8 @@ cudaError_t launch_correlate_tc(const Plan &p, const float *f, const float *h, i
     if (nsm <= 0) nsm = 1;
   }
   const long items = (long)B * (p.LJ / 2 + 1);
-  const int grid = (int)(items < 2L * nsm ? items : 2L * nsm);
+  const long per_sm = p.tune_tc_ctas == 1 ? 1 : 2;
+  const int grid = (int)(items < per_sm * nsm ? items : per_sm * nsm);
   const size_t smem = (size_t)tc_smem(g);
   if (bf16) {
     cudaFuncSetAttribute(k_correlate_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

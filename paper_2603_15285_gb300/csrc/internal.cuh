@@ -16,6 +16,10 @@ struct Plan {
   bool fp64;
   int tc;        // contraction on the tensor cores: 0 no, 1 TF32, 2 BF16 (FP32 plans)
   int *dev_err;  // device word: bit 0 = a tensor-core wait reached its limit
+  // tile choices set by matcha_plan_autotune (0 = the built-in rule); none of
+  // them changes any result bit
+  int tune_shells = 0;   // shells per analysis CTA (1, 2, 4, 8)
+  int tune_tc_ctas = 0;  // tensor-core contraction CTAs per SM (1, 2)
   int nt, np, nlm, npairs, npairs0, ns;
   int ngroups;  // partner groups of the correlation layout, (L_J+1)(L_J+2)/2
   long nc;      // pair slots x degrees per particle (dummy halves included), 4 reals each
@@ -97,6 +101,7 @@ cudaError_t launch_correlate_tc(const Plan &p, const float *f, const float *h, i
 bool correlate_tc_fits(int S, int L, int bytes);
 bool backward_fits(const Plan &p);  // the template-gradient kernel's shared memory fits
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
+bool analyze_shells_ok(const Plan &p, int G);  // G shells per analysis CTA fit
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
 cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
                                 const double *cand_euler, const double *cand_score,

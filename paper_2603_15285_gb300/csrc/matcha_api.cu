@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+#include <functional>
 #include <vector>
 #include "internal.cuh"
 
@@ -425,6 +426,85 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
   CK(cudaMemcpyAsync(best_p, iout, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(flags, iout + B, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return MATCHA_OK;
+}
+
+// Autotuning of the tile choices that leave every result bit unchanged.
+static float time_ms(cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps,
+                     const std::function<cudaError_t()> &fn, cudaError_t *err) {
+  *err = fn();  // warm-up (and attribute setup)
+  if (*err != cudaSuccess) return -1.0f;
+  float best = -1.0f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, st);
+    *err = fn();
+    cudaEventRecord(e1, st);
+    if (*err == cudaSuccess) *err = cudaEventSynchronize(e1);
+    if (*err != cudaSuccess) return -1.0f;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best) best = ms;
+  }
+  return best;
+}
+
+matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles, const float *templates,
+                                   int B, int tstride, void *ws, size_t ws_bytes, void *stream,
+                                   matcha_tune_report *rep) {
+  if (!plan || B < 1 || !valid_stride(tstride) || !particles || !templates || !ws || !rep)
+    return MATCHA_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+  size_t need;
+  matcha_status s = matcha_workspace_size(plan, B, &need);
+  if (s) return s;
+  if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
+  Plan *p = P_(plan);
+  AlignWs w;
+  carve_align(*p, B, tstride ? B : 1, (char *)ws, &w);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t err = cudaSuccess;
+  memset(rep, 0, sizeof(*rep));
+  const int cand[4] = {1, 2, 4, 8};
+  int bestG = 0;
+  float bestT = -1.0f;
+  for (int i = 0; i < 4; ++i) {
+    rep->analyze_ms[i] = -1.0f;
+    if (!analyze_shells_ok(*p, cand[i])) continue;
+    p->tune_shells = cand[i];
+    float t = time_ms(st, e0, e1, 3, [&]() {
+      return p->fp64 ? launch_analyze<double>(*p, particles, B, (double *)w.f, st)
+                     : launch_analyze<float>(*p, particles, B, (float *)w.f, st);
+    }, &err);
+    if (err != cudaSuccess) break;
+    rep->analyze_ms[i] = t;
+    if (bestT < 0 || t < bestT) { bestT = t; bestG = cand[i]; }
+  }
+  p->tune_shells = bestG;
+  rep->analyze_shells = bestG;
+  if (err == cudaSuccess && p->tc) {
+    const int Bt = tstride ? B : 1;
+    err = launch_analyze<float>(*p, particles, B, (float *)w.f, st);
+    if (err == cudaSuccess) err = launch_analyze<float>(*p, templates, Bt, (float *)w.h, st);
+    int bestC = 0;
+    float bc = -1.0f;
+    for (int k = 1; k <= 2 && err == cudaSuccess; ++k) {
+      p->tune_tc_ctas = k;
+      float t = time_ms(st, e0, e1, 3, [&]() {
+        return launch_correlate<float>(*p, (const float *)w.f, (const float *)w.h, B, tstride,
+                                       (float *)w.c, st);
+      }, &err);
+      rep->tc_ms[k - 1] = t;
+      if (err == cudaSuccess && (bc < 0 || t < bc)) { bc = t; bestC = k; }
+    }
+    p->tune_tc_ctas = bestC;
+    rep->tc_ctas_per_sm = bestC;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail_cuda(err, "autotune");
   return MATCHA_OK;
 }
 

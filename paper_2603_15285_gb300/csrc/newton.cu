@@ -541,18 +541,17 @@ __device__ __forceinline__ void wrap_d(double *v) {
   v[0] = mod2pi_d(a); v[1] = b; v[2] = mod2pi_d(g);
 }
 
-// Newton direction from grad g and Hessian H (row-major 3x3) in the working
+// Newton direction from grad g and Hessian H (row-major 3x3) in the solve
 // precision S; returns flag bits.  A Cholesky pivot of -H counts as positive
-// above piv_rel ||H||_F (1e-12 in FP64, 1e-6 in FP32: above the rounding
-// level of H's entries).
+// above piv_rel ||H||_F, set by the precision H was summed in (1e-12 for FP64
+// sums, 1e-6 for FP32 sums: above the rounding level of H's entries).
 template <typename S>
-__device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d) {
-  const S piv_rel = sizeof(S) == 8 ? S(1e-12) : S(1e-6);
+__device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d, double piv_rel) {
   S hn = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
   hn = sqrt(hn);
-  const S tol = piv_rel * hn;
+  const S tol = S(piv_rel) * hn;
   // Cholesky of A = -H
   S a00 = -H[0], a10 = -H[3], a20 = -H[6], a11 = -H[4], a21 = -H[7], a22 = -H[8];
   bool ok = a00 > tol;
@@ -593,11 +592,12 @@ __device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d) {
 }
 
 // Candidate tid has C, grad, H of its current point in res: record C, stop on
-// a non-finite value (flag bit 0), take the Newton direction (in the working
+// a non-finite value (flag bit 0), take the Newton direction (solved in
 // precision S), stop the level when the increment is below step_tol, else
 // prepare the first trial (angles in FP64).
 template <typename S>
-__device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm) {
+__device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, SmemLayout &sm,
+                                           double piv_rel) {
   const double *r = sm.res + 10 * tid;
   const double C = r[0];
   const S g[3] = {S(r[1]), S(r[2]), S(r[3])};
@@ -612,7 +612,7 @@ __device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, 
     return;
   }
   S d[3];
-  sm.fl[tid] |= newton_dir<S>(g, H, L, d);
+  sm.fl[tid] |= newton_dir<S>(g, H, L, d, piv_rel);
   if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < S(A.tol)) {
     sm.state[tid] = ST_STOP;
     return;
@@ -673,6 +673,7 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
   }
   __syncthreads();
   const T *cb = c + 4 * b * A.nc;
+  const double piv_rel = sizeof(T) == 8 ? 1e-12 : 1e-6;  // H summed in T
   long long work_full = 0, work_val = 0;  // counted by thread 0
 
   // A trial point that is accepted is where the next step needs C, grad and
@@ -691,9 +692,15 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
     if (tid == 0)
       for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
     evaluate<T, true>(A, L, cb, rcoef, seedK, sm.th, need, sm);
+    // the 3x3 solves of the final level run in FP64 in every plan
+    const bool last = lev == A.nlev - 1;
+    auto step_from = [&]() {
+      if (last) start_step<double>(tid, L, A, sm, piv_rel);
+      else start_step<T>(tid, L, A, sm, piv_rel);
+    };
     if (tid < P && need[tid]) {
       sm.steps[tid] = 0;
-      start_step<T>(tid, L, A, sm);
+      step_from();
     }
     for (int round = 0; round < 3 * A.M; ++round) {
       int tw = 0, wf = 0;
@@ -715,7 +722,7 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
           sm.Cc[tid] = Ct;
           if (sm.steps[tid] < A.M - 1) {
             ++sm.steps[tid];
-            start_step<T>(tid, L, A, sm);  // derivatives at the accepted point
+            step_from();  // derivatives at the accepted point
           } else {
             sm.state[tid] = ST_STOP;
           }

@@ -41,3 +41,60 @@ def align_groups(groups):
     for s in streams:
         caller.wait_stream(s)
     return results
+
+
+class MixedBatch:
+    """A mixed batch bound to fixed device buffers.
+
+    Each group gets its workspace and outputs once; with ``autotune`` each
+    group's plan is tuned on its own data first (``Plan.autotune``: tile
+    choices that change no result bit).  ``run()`` launches the groups
+    eagerly (concurrent streams, costliest first); ``capture()`` records that
+    launch sequence, fork and join included, into one CUDA graph that
+    ``replay()`` relaunches on the current stream.
+    """
+
+    def __init__(self, groups, autotune: bool = True):
+        import torch
+        from . import alloc_workspace
+        self.groups = []
+        self.tune = []
+        for g in groups:
+            plan, parts = g["plan"], g["particles"]
+            B = parts.shape[0]
+            d = dict(g)
+            d["ws"] = alloc_workspace(plan, B)
+            dev = parts.device
+            d["out"] = dict(euler=torch.empty((B, 3), dtype=torch.float64, device=dev),
+                            R=torch.empty((B, 3, 3), dtype=torch.float64, device=dev),
+                            score=torch.empty((B,), dtype=torch.float64, device=dev),
+                            best_p=torch.empty((B,), dtype=torch.int32, device=dev),
+                            flags=torch.empty((B,), dtype=torch.int32, device=dev))
+            self.tune.append(plan.autotune(parts, g["templates"], ws=d["ws"]) if autotune else None)
+            self.groups.append(d)
+        self.graph = None
+
+    @property
+    def outputs(self):
+        return [g["out"] for g in self.groups]
+
+    def run(self):
+        return align_groups(self.groups)
+
+    def capture(self):
+        import torch
+        self.run()  # first calls on every plan happen outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(graph, stream=cs):
+                align_groups(self.groups)
+        torch.cuda.current_stream().wait_stream(cs)
+        self.graph = graph
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs

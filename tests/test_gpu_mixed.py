@@ -79,3 +79,32 @@ def test_group_launcher_matches_one_call_per_group(groups):
     for n, r in zip(names, res):
         for k in single[n]:
             assert torch.equal(r[k], single[n][k]), (n, k)
+
+
+def test_tuned_graph_replay_matches_untuned_eager(groups):
+    """Autotuned plans replayed from one CUDA graph give bit-identical results
+    to untuned plans launched eagerly (tuning picks only result-invariant tile
+    shapes)."""
+    names = list(groups)
+    ref = {}
+    for n in names:
+        plan = m.plan_for_workload(groups[n]["w"], precision=m.FP32)
+        out = m.matcha_align(plan, groups[n]["particles"], groups[n]["templates"], P_per=groups[n]["P_per"])
+        ref[n] = {k: v.clone() for k, v in out.items()}
+    for prec in (m.FP32, m.TF32):
+        mb = mixed.MixedBatch([dict(plan=m.plan_for_workload(groups[n]["w"], precision=prec),
+                                    particles=groups[n]["particles"], templates=groups[n]["templates"],
+                                    P_per=groups[n]["P_per"]) for n in names], autotune=True)
+        print("autotune (%s):" % ("fp32" if prec == m.FP32 else "tf32"), mb.tune)
+        eager = [{k: v.clone() for k, v in o.items()} for o in mb.run()]
+        mb.capture()
+        for o in mb.outputs:
+            for v in o.values():
+                v.zero_()
+        outs = mb.replay()
+        torch.cuda.synchronize()
+        for n, e, r in zip(names, eager, outs):
+            for k in e:
+                assert torch.equal(r[k], e[k]), (prec, n, k)
+                if prec == m.FP32:
+                    assert torch.equal(r[k], ref[n][k]), (n, k)
