@@ -129,11 +129,16 @@ matcha_status matcha_plan_create(const matcha_plan_desc *desc, matcha_plan *out)
 /* Frees the plan's tables; NULL is accepted. Synchronises the device. */
 matcha_status matcha_plan_destroy(matcha_plan plan);
 matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info);
-/* Reads (synchronously) the plan's device status word: bit 0 is set when a
- * tensor-core kernel's wait for its MMAs reached its iteration limit (its
- * output block is then left unwritten).  Returns MATCHA_ERR_TIMEOUT when any
- * bit is set, else MATCHA_OK. */
+/* Reads (synchronously) and clears the plan's device status word: bit 0 is
+ * set when a tensor-core kernel's wait for its MMAs reached its iteration
+ * limit (that CTA then waits, again bounded, for the MMAs it issued, frees its
+ * tensor memory and stops; the output blocks it had not written stay
+ * unwritten).  Returns MATCHA_ERR_TIMEOUT when any bit was set, else MATCHA_OK. */
 matcha_status matcha_plan_device_status(matcha_plan plan, int *bits);
+/* Sets the number of mbarrier polls after which such a wait gives up (-1
+ * restores the built-in limit, 2^24 polls).  For tests of the timeout path:
+ * with 0 every wait gives up at once. */
+matcha_status matcha_plan_set_wait_limit(matcha_plan plan, long polls);
 
 /* Copies one of the plan's FP64 quadrature tables to the host (synchronous):
  * which = 0 radial nodes r_s, 1 radial weights w_s (r^2 Jacobian included),

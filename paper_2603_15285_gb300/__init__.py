@@ -29,7 +29,7 @@ SYMBOLS = [
     "matcha_newton_march", "matcha_final_select", "matcha_align", "matcha_host_workspace_size",
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
     "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
-    "matcha_plan_device_status", "matcha_plan_autotune",
+    "matcha_plan_device_status", "matcha_plan_autotune", "matcha_plan_set_wait_limit",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
             "matcha_align_host": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_template_grad_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
             "matcha_plan_device_status": [_vp, ctypes.POINTER(i)],
+            "matcha_plan_set_wait_limit": [_vp, l],
             "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
         }
@@ -199,8 +200,13 @@ class Plan:
         return dict(analyze_shells=rep.analyze_shells, analyze_ms=list(rep.analyze_ms),
                     tc_ctas_per_sm=rep.tc_ctas_per_sm, tc_ms=list(rep.tc_ms))
 
+    def set_wait_limit(self, polls: int):
+        """Polls before a tensor-core wait gives up (-1: built-in; 0: at once, for tests)."""
+        _check(lib().matcha_plan_set_wait_limit(self.handle, polls), "matcha_plan_set_wait_limit")
+
     def device_status(self) -> int:
-        """The plan's device status bits (bit 0: a tensor-core wait hit its limit)."""
+        """Reads and clears the plan's device status bits (bit 0: a tensor-core
+        wait hit its limit)."""
         bits = ctypes.c_int(0)
         lib().matcha_plan_device_status(self.handle, ctypes.byref(bits))
         return bits.value

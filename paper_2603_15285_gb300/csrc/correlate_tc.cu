@@ -138,7 +138,7 @@ template <int BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_correlate_tc(const float *__restrict__ f, const float *__restrict__ h, int S, int L,
                    long h_stride, const double *__restrict__ wrad, long nc, float *__restrict__ c,
-                   int B, int *__restrict__ err) {
+                   int B, int *__restrict__ err, long wait_limit) {
   using O = Op<BF16>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
@@ -264,12 +264,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = tmem_base;
   if (tid == 0 && nmine > 0) issue(0);
 
-  int ok = 1;
+  int ok = 1, fail_i = -1;
   for (int i = 0; i < nmine && ok; ++i) {
     const long it = first + (long)i * gridDim.x;
     if (i + 1 < nmine) stage(it + gridDim.x, (i + 1) & 1);
     uint32_t done = 0;
-    for (long w = 0; w < TC_WAIT_LIMIT && !done; ++w)
+    for (long w = 0; w < wait_limit && !done; ++w)
       asm volatile(
           "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
           "selp.u32 %0, 1, 0, p;\n\t}\n"
@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     float *Dt = reinterpret_cast<float *>(bufp(i));  // MMAs of item i are done with it
     if (__syncthreads_and(done) == 0) {
       ok = 0;
+      fail_i = i;
       break;
     }
     if (32 * (warp & 3) < G.RA) {
@@ -353,7 +354,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncthreads();  // the accumulator copy and the buffer are free for item i + 2
   }
-  if (!ok && tid == 0) atomicOr(err, 1);
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 1);
+    // the MMAs of item fail_i are still in flight: wait for them (bounded)
+    // before the columns they write are freed
+    uint32_t done = 0;
+    for (long w = 0; w < TC_WAIT_LIMIT && !done; ++w)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(done)
+          : "r"(su32(&mbar)), "r"((uint32_t)(fail_i & 1))
+          : "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -379,14 +392,15 @@ cudaError_t launch_correlate_tc(const Plan &p, const float *f, const float *h, i
   const long per_sm = p.tune_tc_ctas == 1 ? 1 : 2;
   const int grid = (int)(items < per_sm * nsm ? items : per_sm * nsm);
   const size_t smem = (size_t)tc_smem(g);
+  const long wait_limit = p.wait_limit >= 0 ? p.wait_limit : TC_WAIT_LIMIT;
   if (bf16) {
     cudaFuncSetAttribute(k_correlate_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_correlate_tc<1><<<grid, TC_THREADS, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad, p.nc, c, B,
-                                                      p.dev_err);
+                                                      p.dev_err, wait_limit);
   } else {
     cudaFuncSetAttribute(k_correlate_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_correlate_tc<0><<<grid, TC_THREADS, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad, p.nc, c, B,
-                                                      p.dev_err);
+                                                      p.dev_err, wait_limit);
   }
   return cudaGetLastError();
 }

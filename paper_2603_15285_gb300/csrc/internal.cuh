@@ -20,6 +20,7 @@ struct Plan {
   // them changes any result bit
   int tune_shells = 0;   // shells per analysis CTA (1, 2, 4, 8)
   int tune_tc_ctas = 0;  // tensor-core contraction CTAs per SM (1, 2)
+  long wait_limit = -1;  // mbarrier polls before a wait gives up (-1: the built-in limit)
   int nt, np, nlm, npairs, npairs0, ns;
   int ngroups;  // partner groups of the correlation layout, (L_J+1)(L_J+2)/2
   long nc;      // pair slots x degrees per particle (dummy halves included), 4 reals each

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+#include <nvtx3/nvToolsExt.h>
 #include <functional>
 #include <vector>
 #include "internal.cuh"
@@ -25,6 +26,13 @@ matcha_status fail_cuda(cudaError_t e, const char *where) {
   } while (0)
 
 Plan *P_(matcha_plan p) { return reinterpret_cast<Plan *>(p); }
+
+// NVTX range over one step's enqueue (visible in timeline profilers; no cost
+// without one attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 size_t real_size(const Plan &p) { return p.fp64 ? 8 : 4; }
 
@@ -201,7 +209,14 @@ matcha_status matcha_plan_device_status(matcha_plan plan, int *bits) {
   if (!plan || !bits) return MATCHA_ERR_INVALID_ARG;
   Plan *p = P_(plan);
   CK(cudaMemcpy(bits, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*bits) CK(cudaMemset(p->dev_err, 0, sizeof(int)));
   return *bits ? MATCHA_ERR_TIMEOUT : MATCHA_OK;
+}
+
+matcha_status matcha_plan_set_wait_limit(matcha_plan plan, long polls) {
+  if (!plan || polls < -1) return MATCHA_ERR_INVALID_ARG;
+  P_(plan)->wait_limit = polls;
+  return MATCHA_OK;
 }
 
 matcha_status matcha_plan_info(matcha_plan plan, matcha_plan_info_t *info) {
@@ -330,10 +345,18 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   size_t need = carve_align(*p, B, Bt, (char *)ws, &w);
   if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
   matcha_status s;
-  if ((s = matcha_analyze(plan, particles, B, w.f, stream))) return s;
-  if ((s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
-  if ((s = matcha_correlate_coeffs(plan, w.f, w.h, B, tstride, w.c, stream))) return s;
+  Range all("matcha_align");
   {
+    Range r("a1+a2 analysis");
+    if ((s = matcha_analyze(plan, particles, B, w.f, stream))) return s;
+    if ((s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
+  }
+  {
+    Range r("a3 contraction");
+    if ((s = matcha_correlate_coeffs(plan, w.f, w.h, B, tstride, w.c, stream))) return s;
+  }
+  {
+    Range r("a4+a5 SOFFT search");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = p->fp64 ? launch_soft<double>(*p, (const double *)w.c, B, P_per,
                                                   (double *)w.grid, w.cidx, w.ceuler, w.cscore,
@@ -342,9 +365,13 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
                                                  w.cidx, w.ceuler, w.cscore, w.ncand, st);
     if (e != cudaSuccess) return fail_cuda(e, "soft_search");
   }
-  if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags, nullptr,
-                               stream)))
-    return s;
+  {
+    Range r("a6 Newton march");
+    if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags, nullptr,
+                                 stream)))
+      return s;
+  }
+  Range r("a7 final selection");
   return matcha_final_select(plan, B, P_per, w.ncand, w.ceuler, w.cscore, w.cflags, euler, R, score,
                              best_p, flags, stream);
 }

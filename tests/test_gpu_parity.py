@@ -280,3 +280,20 @@ def test_align_replays_in_a_cuda_graph():
         torch.cuda.synchronize()
         for k in eager:
             assert torch.equal(out[k], eager[k]), (rep, k)
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.FP32, m.TF32])
+def test_poisoned_workspace_gives_the_same_results(prec):
+    """A workspace filled with NaN bit patterns (0xFF bytes) before the call
+    gives bit-identical results: no kernel reads workspace it has not written."""
+    d, parts, temps = gen(SMALL)
+    plan = m.plan_for_workload(SMALL, precision=prec)
+    ws = m.alloc_workspace(plan, parts.shape[0])
+    ws.zero_()
+    ref = {k: v.clone() for k, v in m.matcha_align(plan, parts, temps, ws=ws).items()}
+    ws.fill_(255)
+    out = m.matcha_align(plan, parts, temps, ws=ws)
+    torch.cuda.synchronize()
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
+    assert plan.device_status() == 0

@@ -90,3 +90,30 @@ def test_tc_path_within_005_degrees_of_fp64(batch, fp64_R, prec):
 def test_tc_plan_rejects_bandwidth_64():
     with pytest.raises(m.MatchaError):
         m.Plan(box_n=64, n_shells=32, L0=8, K=2, P=16, M_iter=3, L_sched=[8, 64], precision=m.TF32)
+
+
+def test_forced_wait_timeout_sets_status_and_recovers(batch):
+    """With a wait limit of 0 polls every CTA gives up on its first MMA wait:
+    the status word reports it (and is cleared by the read), the CTAs drain
+    their MMAs and free their tensor memory, and the next call with the
+    built-in limit is correct again."""
+    B = 8
+    parts = batch["particles"][:B].contiguous()
+    temps = batch["templates"][:B].contiguous()
+    plan = m.plan_for_workload(W, precision=m.TF32)
+    f = m.matcha_analyze(plan, parts)
+    h = m.matcha_analyze(plan, temps)
+    good = m.matcha_correlate_coeffs(plan, f, h, 1)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    plan.set_wait_limit(0)
+    m.matcha_correlate_coeffs(plan, f, h, 1)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 1
+    assert plan.device_status() == 0  # cleared by the read
+    plan.set_wait_limit(-1)
+    again = m.matcha_correlate_coeffs(plan, f, h, 1)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    assert torch.equal(again, good)
+    plan.close()
