@@ -140,6 +140,48 @@ def newton_traffic(B):
     return meta["dram_bytes_per_launch_1024"] * B / 1024.0
 
 
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
+    """Achieved fraction of each step's bound, from the event-timed stages and
+    the algorithmic work per particle (volume bytes for the analysis, 8 S T(L)
+    flops for the contraction, grid points for the SOFFT search)."""
+    pk = measured_peaks()
+    hbm = pk["hbm_gbs"]
+    L, S, N = w.L_sched[-1], w.n_shells, w.N
+    T = (L + 1) * (2 * L + 1) * (2 * L + 3) // 3
+    vol_bytes = 2 * 4 * N ** 3 * B  # particle + template volumes, read once
+    out = {"analysis": {"kernel": "k_analyze2 (x2)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
+                        "achieved": vol_bytes / (stage_ms["analyze"] * 1e-3) / 1e9}}
+    out["analysis"]["frac"] = out["analysis"]["achieved"] / hbm
+    flops = 8.0 * S * T * B
+    if prec in (m.TF32, m.BF16):
+        tpk = pk["bf16_tflops"] * (1.0 if prec == m.BF16 else 1.1 / 2.25)
+        src = "measured bf16 burst" + ("" if prec == m.BF16 else " x 1.1/2.25 (nominal TF32/BF16 ratio)")
+        out["contraction"] = {"kernel": "k_correlate_tc", "bound": "tensor", "unit": "TFLOP/s",
+                              "peak": tpk, "peak_source": src}
+    else:
+        out["contraction"] = {"kernel": "k_correlate_deg", "bound": "alu", "unit": "TFLOP/s",
+                              "peak": alu_peak, "peak_source": "derived ALU peak (see roofline)"}
+    c = out["contraction"]
+    c["achieved"] = flops / (stage_ms["correlate"] * 1e-3) / 1e12
+    c["frac"] = c["achieved"] / c["peak"]
+    # bytes the contraction must move: f, h (complex S x n_lm) and c (grouped entries)
+    rb = 8 if prec == m.FP64 else 4
+    nlm = (L + 1) * (L + 2) // 2
+    ge = sum((mm + 1) * (L - mm + 1) for mm in range(L + 1))
+    c["hbm_frac"] = (2 * S * nlm * 2 * rb + 8 * ge * rb) * B / (stage_ms["correlate"] * 1e-3) / 1e9 / hbm
+    n = 2 * w.K * (w.L0 + 1)
+    out["soft"] = {"kernel": "k_soft_chunk", "grid_points_per_s": n ** 3 * B / (stage_ms["soft"] * 1e-3)}
+    out["peaks_file"] = pk.get("source", "MEASURED_PEAKS.json")
+    return out
+
+
 def time_backward(st, reps=5):
     """Template gradient of the refined scores on the shared-template 64^3
     workload (512 particles, L 8 -> 32): forward (a1..a7 from the template's
@@ -407,6 +449,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
     }
+    res["kernel_roofline"] = kernel_roofline(w, B, prec, stage_ms, peak, m)
     # accuracy of the timed path against the FP64 GPU path (oracle-checked in the tests)
     if rank == 0 and not args.no_fp64 and is32:
         plan64 = m.plan_for_workload(w, precision=m.FP64)
