@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
     return ap.parse_args()
 
@@ -255,6 +256,46 @@ def time_mixed(st, prec, reps=5):
             "unit": "particles/s", "timed": "one CUDA graph of all groups, replayed",
             "autotune": [{"shells_per_analysis_cta": t["analyze_shells"],
                           "tc_ctas_per_sm": t["tc_ctas_per_sm"]} for t in mb.tune]}
+
+
+def time_paper_scale(st, reps=3):
+    """The paper's own regime (200^3 boxes, 40 shells, SOFFT at L0 = 30 with
+    K = 2, P = 10, one Newton step per band, L 30 -> 40, 0 dB): FP32 and FP64
+    plans, eager matcha_align, errors against FP64 and the planted rotation."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2603_15285_gb300 as m
+    import synth
+    w = synth.WORKLOADS["paper200"]
+    d = synth.make_batch(w, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    B = parts.shape[0]
+    out = {"workload": "paper200: %d particles of 200^3, 40 shells, L0=30 K=2 (124^3 grid), P=10, "
+                       "L 30->40, one Newton step per band, SNR 1 (0 dB), +-60 deg wedge" % B}
+    Rs = {}
+    for name, prec in (("fp32", m.FP32), ("fp64", m.FP64)):
+        plan = m.plan_for_workload(w, precision=prec)
+        ws = m.alloc_workspace(plan, B)
+        o = m.matcha_align(plan, parts, temps, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            m.matcha_align(plan, parts, temps, ws=ws, out=o)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "value": B / (ms * 1e-3), "unit": "particles/s"}
+        Rs[name] = o["R"].cpu().numpy()
+        del ws
+        plan.close()
+    e = np.degrees([oracle.rotation_angle(Rs["fp32"][b], Rs["fp64"][b]) for b in range(B)])
+    t = np.degrees([oracle.rotation_angle(Rs["fp64"][b], d["R_true"][b]) for b in range(B)])
+    out["fp32_vs_fp64_deg"] = {"max": float(e.max()), "p90": float(np.percentile(e, 90))}
+    out["fp64_vs_planted_deg"] = {"median": float(np.median(t)), "p90": float(np.percentile(t, 90)),
+                                  "max": float(t.max())}
+    return out
 
 
 def run_reference(args):
@@ -528,6 +569,10 @@ def main():
         res["backward"] = time_backward(st)
     if rank == 0 and not args.no_mixed:
         res["mixed"] = time_mixed(st, prec)
+        import torch
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_paper:
+        res["paper_scale"] = time_paper_scale(st)
         import torch
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:

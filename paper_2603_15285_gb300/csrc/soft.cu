@@ -53,34 +53,47 @@ k_soft_grid(const T *__restrict__ c, long nc, int L0, int ns, const int *__restr
     if (n != m && n != -m) { put(n, m, br, bi); put(-n, -m, br, -bi); }
   }
   __syncthreads();
-  // G_m(j) = sum_n S_mn e^{i n g_j}, m = 0..L0
+  // G_m(j) = sum_n S_mn e^{i n g_j}, m = 0..L0; the twiddle index n j mod ns
+  // advances by j per term (no integer division in the loop)
   for (int idx = threadIdx.x; idx < (L0 + 1) * ns; idx += blockDim.x) {
     int m = idx / ns, j = idx - m * ns;
     T re = 0, im = 0;
     const T *row = Sg + 2 * (m + L0) * W;
-    for (int n = -L0; n <= L0; ++n) {
-      int t = (int)(((long)n * j) % ns);
-      if (t < 0) t += ns;
+    int t = (int)(((long)(ns - j) * L0) % ns);  // (-L0 j) mod ns
+    for (int n = 0; n < W; ++n) {
       T cr = tw[2 * t], ci = tw[2 * t + 1];
-      T sr = row[2 * (n + L0)], si = row[2 * (n + L0) + 1];
+      T sr = row[2 * n], si = row[2 * n + 1];
       re += sr * cr - si * ci;
       im += sr * ci + si * cr;
+      t += j;
+      if (t >= ns) t -= ns;
     }
     G[2 * idx] = re;
     G[2 * idx + 1] = im;
   }
   __syncthreads();
-  // C(i, k, j) = Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m a_i}
+  // C(i, k, j) = Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m a_i}; four alpha
+  // rows per thread share each G_m(j) load
   T *gb = grid + b * (long)ns * ns * ns;
-  for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
-    int i = idx / ns, j = idx - i * ns;
-    T acc = 0;
+  const int ni4 = (ns + 3) / 4;
+  for (int idx = threadIdx.x; idx < ni4 * ns; idx += blockDim.x) {
+    const int i0 = 4 * (idx / ns), j = idx - (idx / ns) * ns;
+    T acc[4] = {0, 0, 0, 0};
+    int t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t[u] = i0 + u < ns ? i0 + u : 0;  // m i mod ns at m = 1
     for (int m = 1; m <= L0; ++m) {
-      int t = (int)(((long)m * i) % ns);
-      T gr = G[2 * (m * ns + j)], gi = G[2 * (m * ns + j) + 1];
-      acc += gr * tw[2 * t] - gi * tw[2 * t + 1];
+      const T gr = G[2 * (m * ns + j)], gi = G[2 * (m * ns + j) + 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc[u] += gr * tw[2 * t[u]] - gi * tw[2 * t[u] + 1];
+        t[u] += i0 + u;
+        if (t[u] >= ns) t[u] -= ns;
+      }
     }
-    gb[((long)i * ns + k) * ns + j] = G[2 * j] + 2 * acc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < ns) gb[((long)(i0 + u) * ns + k) * ns + j] = G[2 * j] + 2 * acc[u];
   }
 }
 
@@ -120,9 +133,16 @@ __device__ __forceinline__ bool is_local_max(const T *__restrict__ g, int ns, in
   return true;
 }
 
-constexpr int TOPK_CAP = 3072;
-constexpr int TOPK_THREADS = 512;
+constexpr int TOPK_THREADS = 1024;
 
+// Top-P local maxima of a materialised grid, one CTA per particle.  One warp
+// per grid row (alpha i, beta k), lanes along gamma, so every neighbour load
+// is coalesced; the test is the (value, index) order of is_local_max, the
+// point's own row first, each lane stopping at its first failure.  Each warp
+// keeps the best P_max maxima it has seen as a sorted list distributed over
+// its lanes (lane r holds rank r), inserting a new maximum only when it
+// precedes the list's last entry; the warp lists are merged at the end.  All
+// maxima are counted, for n_cand.
 template <typename T>
 __global__ void __launch_bounds__(TOPK_THREADS)
 k_topk(const T *__restrict__ grid, int ns, int P_max, const int *__restrict__ P_per,
@@ -131,53 +151,106 @@ k_topk(const T *__restrict__ grid, int ns, int P_max, const int *__restrict__ P_
   const long b = blockIdx.x;
   const int tot = ns * ns * ns;
   const T *g = grid + b * (long)tot;
+  constexpr int NW = TOPK_THREADS / 32;
   __shared__ int cnt;
-  __shared__ T lv[TOPK_CAP];
-  __shared__ int li[TOPK_CAP];
-  __shared__ T red_v[TOPK_THREADS / 32];
-  __shared__ int red_i[TOPK_THREADS / 32];
+  __shared__ T lv[NW * 32];
+  __shared__ int li[NW * 32];
+  __shared__ T red_v[NW];
+  __shared__ int red_i[NW];
   __shared__ T prev_v;
   __shared__ int prev_i;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  for (int p = threadIdx.x; p < tot; p += blockDim.x) {
-    if (is_local_max(g, ns, p)) {
-      int pos = atomicAdd(&cnt, 1);
-      if (pos < TOPK_CAP) { lv[pos] = g[p]; li[pos] = p; }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T wv = T(0);
+  int wi = INT_MAX;  // this lane's rank of the warp list (INT_MAX: empty)
+  int found = 0;
+  for (int ik = warp; ik < ns * ns; ik += NW) {
+    const int i = ik / ns, k = ik - i * ns;
+    const int im = i == 0 ? ns - 1 : i - 1, ip = i == ns - 1 ? 0 : i + 1;
+    const int base = (i * ns + k) * ns;
+    // four 32-point chunks of the row at once: four independent load chains
+    for (int j00 = 0; j00 < ns; j00 += 128) {
+      bool ok[4];
+      T v[4];
+      int jj[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        jj[c] = j00 + 32 * c + lane;
+        ok[c] = jj[c] < ns;
+        v[c] = ok[c] ? g[base + jj[c]] : T(0);
+        ok[c] = ok[c] && v[c] == v[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = jj[c], p = base + j;
+        const int jm = j == 0 ? ns - 1 : j - 1, jp = j >= ns - 1 ? 0 : j + 1;
+        if (ok[c]) ok[c] = precedes(v[c], p, g[base + jm], base + jm) && precedes(v[c], p, g[base + jp], base + jp);
+      }
+#pragma unroll
+      for (int di = 0; di < 3; ++di) {
+        const int ii = di == 0 ? im : (di == 1 ? i : ip);
+#pragma unroll
+        for (int dk = -1; dk <= 1; ++dk) {
+          const int kk = k + dk;
+          if (kk < 0 || kk >= ns || (di == 1 && dk == 0)) continue;
+          const int rb = (ii * ns + kk) * ns;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (!ok[c]) continue;
+            const int j = jj[c], p = base + j;
+            const int jm = j == 0 ? ns - 1 : j - 1, jp = j >= ns - 1 ? 0 : j + 1;
+            ok[c] = precedes(v[c], p, g[rb + j], rb + j) && precedes(v[c], p, g[rb + jm], rb + jm) &&
+                    precedes(v[c], p, g[rb + jp], rb + jp);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        found += ok[c];
+        const int p = base + jj[c];
+        unsigned m = __ballot_sync(0xffffffffu, ok[c]);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const T cv = __shfl_sync(0xffffffffu, v[c], src);
+          const int ci = __shfl_sync(0xffffffffu, p, src);
+          const bool before = lane < P_max && wi != INT_MAX && precedes(wv, wi, cv, ci);
+          const int pos = __popc(__ballot_sync(0xffffffffu, before));
+          const T uv = __shfl_up_sync(0xffffffffu, wv, 1);
+          const int ui = __shfl_up_sync(0xffffffffu, wi, 1);
+          if (pos < P_max) {
+            if (lane > pos && lane < P_max) { wv = uv; wi = ui; }
+            if (lane == pos) { wv = cv; wi = ci; }
+          }
+        }
+      }
     }
   }
+  atomicAdd(&cnt, found);
+  lv[warp * 32 + lane] = wv;
+  li[warp * 32 + lane] = lane < P_max ? wi : INT_MAX;
   __syncthreads();
   const int n_max = cnt;
-  const bool listed = n_max <= TOPK_CAP;
   int Pb = P_per ? min(P_per[b], P_max) : P_max;
   if (Pb < 0) Pb = 0;
   const int kept = min(Pb, n_max);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // merge: rank r is the best entry of the warp lists that follows rank r-1
   for (int r = 0; r < kept; ++r) {
-    T bv = -INFINITY;
+    const bool have_prev = r > 0;
+    const T pv = have_prev ? prev_v : T(0);
+    const int pi = have_prev ? prev_i : 0;
+    T bv = T(0);
     int bi = INT_MAX;
-    bool have_prev = r > 0;
-    T pv = have_prev ? prev_v : T(0);
-    int pi = have_prev ? prev_i : 0;
-    if (listed) {
-      for (int t = threadIdx.x; t < n_max; t += blockDim.x) {
-        T v = lv[t];
-        int i = li[t];
-        if (have_prev && !precedes(pv, pi, v, i)) continue;
-        if (bi == INT_MAX || precedes(v, i, bv, bi)) { bv = v; bi = i; }
-      }
-    } else {
-      for (int p = threadIdx.x; p < tot; p += blockDim.x) {
-        T v = g[p];
-        if (have_prev && !precedes(pv, pi, v, p)) continue;
-        if (bi != INT_MAX && !precedes(v, p, bv, bi)) continue;
-        if (!is_local_max(g, ns, p)) continue;
-        bv = v; bi = p;
-      }
+    for (int t = threadIdx.x; t < NW * 32; t += blockDim.x) {
+      const T v = lv[t];
+      const int i = li[t];
+      if (i == INT_MAX || (have_prev && !precedes(pv, pi, v, i))) continue;
+      if (bi == INT_MAX || precedes(v, i, bv, bi)) { bv = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (oi != INT_MAX && (bi == INT_MAX || precedes(ov, oi, bv, bi))) { bv = ov; bi = oi; }
     }
     if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
@@ -185,7 +258,7 @@ k_topk(const T *__restrict__ grid, int ns, int P_max, const int *__restrict__ P_
     if (threadIdx.x == 0) {
       T v = red_v[0];
       int i = red_i[0];
-      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+      for (int w = 1; w < NW; ++w)
         if (red_i[w] != INT_MAX && (i == INT_MAX || precedes(red_v[w], red_i[w], v, i))) {
           v = red_v[w]; i = red_i[w];
         }
@@ -953,6 +1026,8 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
   }
   int W = 2 * p.L0 + 1;
   size_t smem = sizeof(T) * (2 * (size_t)W * W + 2 * (size_t)(p.L0 + 1) * p.ns);
+  if (smem > 227 * 1024 - 1024) return cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_soft_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_soft_grid<T><<<dim3(p.ns, B), 256, smem, st>>>(c, p.nc, p.L0, p.ns, p.pair_base,
                                                    (const T *)p.soft_d, p.pair_off0, p.nc0,
                                                    (const T *)p.soft_tw, grid);

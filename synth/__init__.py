@@ -103,6 +103,11 @@ WORKLOADS = {
     "grad64": Workload("grad64", B=512, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                        snr=0.2, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
                        L0=8, K=2, P=16, M_iter=3, base_seed=20260320, shared_template=True),
+    # The paper's own regime: 200^3 boxes, SOFFT at L0 = 30 with K = 2 (a 124^3
+    # grid), P = 10 candidates, one Newton step per band, final L = 40, at 0 dB.
+    "paper200": Workload("paper200", B=256, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,
+                         snr=1.0, wedge_deg=60.0, n_shells=40, L_sched=(30, 40),
+                         L0=30, K=2, P=10, M_iter=1, base_seed=20260321),
 }
 
 
