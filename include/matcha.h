@@ -235,7 +235,7 @@ matcha_status matcha_align(matcha_plan plan, const float *particles_dev, const f
 /* matcha_align on HOST buffers: copies the volumes to the device (into the
  * workspace, which must hold matcha_host_workspace_size bytes), runs the
  * path, copies the results back and synchronises the stream.  The batch is
- * split into up to 4 chunks: chunk i+1 is copied on a copy stream owned by
+ * split into up to 8 chunks: chunk i+1 is copied on a copy stream owned by
  * the plan (created on the first call) while chunk i is aligned on `stream`,
  * so host calls on one plan must not run concurrently.  Host buffers may be
  * pageable; pinned buffers give full copy bandwidth and the overlap. */

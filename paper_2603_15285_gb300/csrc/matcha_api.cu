@@ -376,12 +376,13 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
                              best_p, flags, stream);
 }
 
-// Host-buffer path: the batch is split into up to 4 chunks; chunk i+1 is copied
-// to the device on the plan's copy stream while chunk i is aligned on the
-// caller's stream (host-to-device bandwidth, not compute, bounds this path).
+// Host-buffer path: the batch is split into up to 8 chunks (of at least 128
+// particles); chunk i+1 is copied to the device on the plan's copy stream
+// while chunk i is aligned on the caller's stream.  Host-to-device bandwidth
+// bounds this path, so only the last chunk's alignment is exposed.
 static int host_chunk(int B) {
-  int ch = (B + 3) / 4;
-  return ch < 256 ? (B < 256 ? B : 256) : ch;
+  int ch = (B + 7) / 8;
+  return ch < 128 ? (B < 128 ? B : 128) : ch;
 }
 
 matcha_status matcha_host_workspace_size(matcha_plan plan, int B, int tstride, size_t *bytes) {
