@@ -112,32 +112,13 @@ __device__ __forceinline__ bool precedes(T va, int ia, T vb, int ib) {
   return va > vb || (va == vb && ia < ib);
 }
 
-template <typename T>
-__device__ __forceinline__ bool is_local_max(const T *__restrict__ g, int ns, int p) {
-  int i = p / (ns * ns), k = (p / ns) % ns, j = p % ns;
-  T v = g[p];
-  if (v != v) return false;
-  for (int di = -1; di <= 1; ++di) {
-    int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
-    for (int dk = -1; dk <= 1; ++dk) {
-      int kk = k + dk;
-      if (kk < 0 || kk >= ns) continue;
-      for (int dj = -1; dj <= 1; ++dj) {
-        if (!di && !dk && !dj) continue;
-        int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
-        int q = (ii * ns + kk) * ns + jj;
-        if (!precedes(v, p, g[q], q)) return false;
-      }
-    }
-  }
-  return true;
-}
-
 constexpr int TOPK_THREADS = 1024;
 
-// Top-P local maxima of a materialised grid, one CTA per particle.  One warp
-// per grid row (alpha i, beta k), lanes along gamma, so every neighbour load
-// is coalesced; the test is the (value, index) order of is_local_max, the
+// Top-P local maxima of a materialised grid, one CTA per particle.  A point is
+// a local maximum when it precedes each of its 26 neighbours in the order
+// (value desc, index asc), alpha and gamma wrapping and beta neighbours
+// outside the grid skipped; NaN is never one.  One warp per grid row (alpha
+// i, beta k), lanes along gamma, so every neighbour load is coalesced; the
 // point's own row first, each lane stopping at its first failure.  Each warp
 // keeps the best P_max maxima it has seen as a sorted list distributed over
 // its lanes (lane r holds rank r), inserting a new maximum only when it
