@@ -63,6 +63,19 @@ def build(force=False, verbose=False, ptxas_v=False):
         tmp = OUT + ".tmp%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
         os.replace(tmp, OUT)
+    # a C program using the library through its C ABI alone
+    ex_src = os.path.join(HERE, "examples", "align_from_c.c")
+    ex_out = os.path.join(HERE, "_lib", "align_from_c")
+    if force or _stale(ex_out, [ex_src, OUT] + hdeps):
+        cuda = os.path.dirname(os.path.dirname(nvcc)) if os.path.isabs(nvcc) else "/usr/local/cuda"
+        libdir = os.path.join(HERE, "_lib")
+        cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                        if os.path.isdir(d)), os.path.join(cuda, "lib64"))
+        run(["gcc", "-O2", "-std=c11", "-o", ex_out + ".tmp", ex_src,
+             "-I", os.path.join(HERE, "..", "include"), "-I", os.path.join(cuda, "include"),
+             "-L", libdir, "-lmatcha", "-L", cudalib, "-lcudart",
+             "-Wl,-rpath," + libdir, "-Wl,-rpath," + cudalib])
+        os.replace(ex_out + ".tmp", ex_out)
     return OUT
 
 

@@ -297,3 +297,28 @@ def test_poisoned_workspace_gives_the_same_results(prec):
     for k in ref:
         assert torch.equal(out[k], ref[k]), k
     assert plan.device_status() == 0
+
+
+def test_c_program_through_the_c_abi_matches_python(tmp_path):
+    """A C program that links only the library (and the CUDA runtime for its
+    workspace) gives the same results as the Python binding."""
+    import os
+    import subprocess
+    w = synth.WORKLOADS["small32"]
+    d = synth.make_batch(w, B=3)
+    parts, temps = d["particles"].numpy(), d["templates"].numpy()
+    pf, tf = tmp_path / "p.f32", tmp_path / "t.f32"
+    parts.astype(np.float32).tofile(pf)
+    temps.astype(np.float32).tofile(tf)
+    exe = os.path.join(os.path.dirname(m.LIB_PATH), "align_from_c")
+    args = [exe, str(w.N), str(w.n_shells), str(w.L0), str(w.K), str(w.P), str(w.M_iter), "3",
+            str(pf), str(tf)] + [str(L) for L in w.L_sched[1:]]
+    out = subprocess.run(args, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    rows = [line.split() for line in out.stdout.strip().splitlines()]
+    plan = m.plan_for_workload(w, precision=m.FP64)
+    ref = m.matcha_align_host(plan, parts, temps)
+    for b, r in enumerate(rows):
+        assert int(r[1]) == int(ref["best_p"][b])
+        assert float(r[2]) == ref["score"][b]
+        assert [float(x) for x in r[3:6]] == list(ref["euler"][b])
