@@ -103,6 +103,10 @@ WORKLOADS = {
     "grad64": Workload("grad64", B=512, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
                        snr=0.2, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
                        L0=8, K=2, P=16, M_iter=3, base_seed=20260320, shared_template=True),
+    # The largest bandwidth the library takes (L_J = 64), a short batch.
+    "max64": Workload("max64", B=8, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
+                      snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 32, 64),
+                      L0=8, K=2, P=16, M_iter=3, base_seed=20260322),
     # The paper's own regime: 200^3 boxes, SOFFT at L0 = 30 with K = 2 (a 124^3
     # grid), P = 10 candidates, one Newton step per band, final L = 40, at 0 dB.
     "paper200": Workload("paper200", B=256, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,

@@ -52,3 +52,38 @@ def test_deep_fp32_within_005_degrees(batch, fp64_result):
     print("deep64 fp32 vs fp64 GPU: max %.3e deg" % math.degrees(errs.max()))
     assert math.degrees(errs.max()) < 0.05
     assert np.all(np.isfinite(out["score"].cpu().numpy()))
+
+
+def test_max_bandwidth_64_fp64_matches_oracle_and_fp32_within_005():
+    """L_J = 64, the library's limit (schedule 8 -> 16 -> 32 -> 64): FP64 against
+    the oracle on one particle, FP32 within 0.05 degrees of FP64 on the batch."""
+    w = synth.WORKLOADS["max64"]
+    d = synth.make_batch(w, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    p64 = m.plan_for_workload(w, precision=m.FP64)
+    o64 = m.matcha_align(p64, parts, temps)
+    p32 = m.plan_for_workload(w, precision=m.FP32)
+    o32 = m.matcha_align(p32, parts, temps)
+    torch.cuda.synchronize()
+    R64, R32 = o64["R"].cpu().numpy(), o32["R"].cpu().numpy()
+    ref = oracle_align(w, parts[:1].cpu().numpy(), temps[:1].cpu().numpy())
+    assert O.rotation_angle(R64[0], ref["R"][0]) < 1e-8
+    assert abs(o64["score"][0].item() - ref["score"][0]) <= 1e-10 * abs(ref["score"][0])
+    errs = np.degrees([O.rotation_angle(R32[b], R64[b]) for b in range(w.B)])
+    print("max64: fp32 vs fp64 max %.3e deg" % errs.max())
+    assert errs.max() < 0.05
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.FP32])
+def test_zero_volumes_are_degenerate_not_fatal(prec):
+    """All-zero particle and template: C vanishes everywhere, every grid point
+    ties, the Hessian is zero (gradient fallback with a zero step): the call
+    returns, with finite outputs and the ties broken by index."""
+    w = synth.WORKLOADS["small32"]
+    z = torch.zeros((2, w.N, w.N, w.N), dtype=torch.float32, device="cuda")
+    plan = m.plan_for_workload(w, precision=prec)
+    out = m.matcha_align(plan, z, z)
+    torch.cuda.synchronize()
+    assert torch.all(out["score"] == 0)
+    assert torch.all(torch.isfinite(out["euler"]))
+    assert torch.all(out["best_p"] == 0)
