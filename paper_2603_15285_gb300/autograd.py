@@ -31,6 +31,8 @@ def _function_classes():
         @staticmethod
         def backward(ctx, g_score, g_euler):
             f, c, euler = ctx.saved_tensors
+            if g_score is None:  # only the (non-differentiable) rotations were used
+                return None, None, None
             w = g_score.to(T.float64).contiguous()
             g = matcha_template_grad(ctx.plan, f, c, euler, weight=w, template_batch_stride=0)
             return g["vox_grad"][0].to(ctx.tdtype), None, None
@@ -47,6 +49,8 @@ def _function_classes():
         @staticmethod
         def backward(ctx, g_score, g_euler):
             f, c, euler = ctx.saved_tensors
+            if g_score is None:
+                return None, None, None
             w = g_score.to(T.float64).contiguous()
             g = matcha_template_grad(ctx.plan, f, c, euler, weight=w, template_batch_stride=0,
                                      voxels=False)
