@@ -43,6 +43,9 @@ struct Plan {
   // copy stream and events of matcha_align_host (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev[9] = {};
+  // second stream of matcha_align's two half-batches and its fork / join events
+  cudaStream_t split_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }

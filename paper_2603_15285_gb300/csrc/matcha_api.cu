@@ -199,6 +199,9 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
   for (auto &ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->split_stream) cudaStreamDestroy(p->split_stream);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   cudaError_t e = cudaFree(p->base);
   delete p;
   if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
@@ -330,26 +333,20 @@ matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per, con
   return MATCHA_OK;
 }
 
-matcha_status matcha_align(matcha_plan plan, const float *particles, const float *templates, int B,
-                           int tstride, const int *P_per, double *euler, double *R, double *score,
-                           int *best_p, int *flags, void *ws, size_t ws_bytes, void *stream) {
-  if (!plan || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
-  if (B == 0) return MATCHA_OK;
-  if (!particles || !templates || !euler || !R || !score || !best_p || !flags || !ws)
-    return MATCHA_ERR_INVALID_ARG;
-  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
-  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+// Steps a1..a7 for the particle range covered by `w` (workspace arrays already
+// offset to the range's first particle); the templates' coefficients are
+// analysed here unless `h_ready`.
+static matcha_status align_range(matcha_plan plan, const float *particles, const float *templates,
+                                 int B, int tstride, bool h_ready, const int *P_per, double *euler,
+                                 double *R, double *score, int *best_p, int *flags,
+                                 const AlignWs &w, void *stream) {
   Plan *p = P_(plan);
   const int Bt = tstride ? B : 1;
-  AlignWs w;
-  size_t need = carve_align(*p, B, Bt, (char *)ws, &w);
-  if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
   matcha_status s;
-  Range all("matcha_align");
   {
     Range r("a1+a2 analysis");
     if ((s = matcha_analyze(plan, particles, B, w.f, stream))) return s;
-    if ((s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
+    if (!h_ready && (s = matcha_analyze(plan, templates, Bt, w.h, stream))) return s;
   }
   {
     Range r("a3 contraction");
@@ -374,6 +371,72 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   Range r("a7 final selection");
   return matcha_final_select(plan, B, P_per, w.ncand, w.ceuler, w.cscore, w.cflags, euler, R, score,
                              best_p, flags, stream);
+}
+
+// The workspace arrays of `w` advanced to particle b0.
+static AlignWs ws_at(const Plan &p, const AlignWs &w, long b0, int tstride) {
+  const size_t rs = real_size(p), coefv = (size_t)p.S * p.nlm * 2;
+  AlignWs o = w;
+  o.f = (char *)w.f + rs * coefv * b0;
+  o.h = (char *)w.h + rs * coefv * (tstride ? b0 : 0);
+  o.c = (char *)w.c + rs * 4 * (size_t)p.nc * b0;
+  o.grid = w.grid ? (char *)w.grid + rs * (size_t)p.ns * p.ns * p.ns * b0 : nullptr;
+  o.cidx = w.cidx + b0 * p.P;
+  o.cflags = w.cflags + b0 * p.P;
+  o.ncand = w.ncand + b0;
+  o.ceuler = w.ceuler + 3 * b0 * p.P;
+  o.cscore = w.cscore + b0 * p.P;
+  return o;
+}
+
+matcha_status matcha_align(matcha_plan plan, const float *particles, const float *templates, int B,
+                           int tstride, const int *P_per, double *euler, double *R, double *score,
+                           int *best_p, int *flags, void *ws, size_t ws_bytes, void *stream) {
+  if (!plan || B < 0 || !valid_stride(tstride)) return MATCHA_ERR_INVALID_ARG;
+  if (B == 0) return MATCHA_OK;
+  if (!particles || !templates || !euler || !R || !score || !best_p || !flags || !ws)
+    return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  const int Bt = tstride ? B : 1;
+  AlignWs w;
+  size_t need = carve_align(*p, B, Bt, (char *)ws, &w);
+  if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
+  Range all("matcha_align");
+  if (B < 256)
+    return align_range(plan, particles, templates, B, tstride, false, P_per, euler, R, score,
+                       best_p, flags, w, stream);
+  // Two halves on two streams (the caller's and one the plan owns), joined
+  // back into the caller's stream: each half's kernels fill the other's wave
+  // tails.  Every particle's arithmetic is the same as in one pass.
+  if (!p->split_stream) {
+    CK(cudaStreamCreateWithFlags(&p->split_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  }
+  cudaStream_t st = (cudaStream_t)stream, s2 = p->split_stream;
+  matcha_status s;
+  bool h_ready = false;
+  if (!tstride) {  // one shared template: analysed once, before the fork
+    if ((s = matcha_analyze(plan, templates, 1, w.h, stream))) return s;
+    h_ready = true;
+  }
+  CK(cudaEventRecord(p->ev_fork, st));
+  CK(cudaStreamWaitEvent(s2, p->ev_fork, 0));
+  const int B0 = B / 2, B1 = B - B0;
+  const AlignWs w1 = ws_at(*p, w, B0, tstride);
+  const size_t vox = (size_t)p->N * p->N * p->N;
+  if ((s = align_range(plan, particles + vox * B0, tstride ? templates + vox * B0 : templates, B1,
+                       tstride, h_ready, P_per ? P_per + B0 : nullptr, euler + 3 * B0,
+                       R + 9 * B0, score + B0, best_p + B0, flags + B0, w1, s2)))
+    return s;
+  if ((s = align_range(plan, particles, templates, B0, tstride, h_ready, P_per, euler, R, score,
+                       best_p, flags, w, stream)))
+    return s;
+  CK(cudaEventRecord(p->ev_join, s2));
+  CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+  return MATCHA_OK;
 }
 
 // Host-buffer path: the batch is split into up to 8 chunks (of at least 128
