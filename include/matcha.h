@@ -226,7 +226,11 @@ matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per_dev,
  * matcha_workspace_size(plan, B) bytes (256-byte aligned).  The call only
  * enqueues kernels on `stream` (no allocation, no synchronisation), so it can
  * be captured into a CUDA graph and replayed with the same buffers; the first
- * call on a plan should be made before capture. */
+ * call on a plan should be made before capture.  From 256 particles on, the
+ * two halves of the batch run concurrently, one on `stream` and one on a
+ * stream the plan owns (forked from `stream` and joined back into it by
+ * events), so the call's work stays ordered on `stream`; calls on one plan
+ * from several host threads at once share that second stream. */
 matcha_status matcha_align(matcha_plan plan, const float *particles_dev, const float *templates_dev,
                            int B, int template_batch_stride, const int *P_per_dev,
                            double *euler_dev, double *R_dev, double *score_dev, int *best_p_dev,
