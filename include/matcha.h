@@ -227,10 +227,10 @@ matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per_dev,
  * enqueues kernels on `stream` (no allocation, no synchronisation), so it can
  * be captured into a CUDA graph and replayed with the same buffers; the first
  * call on a plan should be made before capture.  From 256 particles on, the
- * two halves of the batch run concurrently, one on `stream` and one on a
- * stream the plan owns (forked from `stream` and joined back into it by
+ * batch runs as up to four concurrent parts, one on `stream` and the others
+ * on streams the plan owns (forked from `stream` and joined back into it by
  * events), so the call's work stays ordered on `stream`; calls on one plan
- * from several host threads at once share that second stream. */
+ * from several host threads at once share those streams. */
 matcha_status matcha_align(matcha_plan plan, const float *particles_dev, const float *templates_dev,
                            int B, int template_batch_stride, const int *P_per_dev,
                            double *euler_dev, double *R_dev, double *score_dev, int *best_p_dev,

@@ -43,9 +43,10 @@ struct Plan {
   // copy stream and events of matcha_align_host (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev[9] = {};
-  // second stream of matcha_align's two half-batches and its fork / join events
-  cudaStream_t split_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // extra streams of matcha_align's concurrent parts and their fork / join events
+  static constexpr int NSPLIT = 4;
+  cudaStream_t split_stream[NSPLIT - 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[NSPLIT - 1] = {};
 };
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }

@@ -199,9 +199,11 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
   for (auto &ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
-  if (p->split_stream) cudaStreamDestroy(p->split_stream);
+  for (int i = 0; i < Plan::NSPLIT - 1; ++i) {
+    if (p->split_stream[i]) cudaStreamDestroy(p->split_stream[i]);
+    if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
+  }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-  if (p->ev_join) cudaEventDestroy(p->ev_join);
   cudaError_t e = cudaFree(p->base);
   delete p;
   if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
@@ -407,35 +409,40 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   if (B < 256)
     return align_range(plan, particles, templates, B, tstride, false, P_per, euler, R, score,
                        best_p, flags, w, stream);
-  // Two halves on two streams (the caller's and one the plan owns), joined
-  // back into the caller's stream: each half's kernels fill the other's wave
-  // tails.  Every particle's arithmetic is the same as in one pass.
-  if (!p->split_stream) {
-    CK(cudaStreamCreateWithFlags(&p->split_stream, cudaStreamNonBlocking));
+  // Parts of at least 128 particles on up to NSPLIT streams (the caller's and
+  // ones the plan owns), joined back into the caller's stream: each part's
+  // kernels fill the others' wave tails.  Every particle's arithmetic is the
+  // same as in one pass.
+  if (!p->ev_fork) {
     CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    for (int i = 0; i < Plan::NSPLIT - 1; ++i) {
+      CK(cudaStreamCreateWithFlags(&p->split_stream[i], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
+    }
   }
-  cudaStream_t st = (cudaStream_t)stream, s2 = p->split_stream;
+  cudaStream_t st = (cudaStream_t)stream;
   matcha_status s;
   bool h_ready = false;
   if (!tstride) {  // one shared template: analysed once, before the fork
     if ((s = matcha_analyze(plan, templates, 1, w.h, stream))) return s;
     h_ready = true;
   }
+  int np = B / 128;
+  if (np > Plan::NSPLIT) np = Plan::NSPLIT;
   CK(cudaEventRecord(p->ev_fork, st));
-  CK(cudaStreamWaitEvent(s2, p->ev_fork, 0));
-  const int B0 = B / 2, B1 = B - B0;
-  const AlignWs w1 = ws_at(*p, w, B0, tstride);
   const size_t vox = (size_t)p->N * p->N * p->N;
-  if ((s = align_range(plan, particles + vox * B0, tstride ? templates + vox * B0 : templates, B1,
-                       tstride, h_ready, P_per ? P_per + B0 : nullptr, euler + 3 * B0,
-                       R + 9 * B0, score + B0, best_p + B0, flags + B0, w1, s2)))
-    return s;
-  if ((s = align_range(plan, particles, templates, B0, tstride, h_ready, P_per, euler, R, score,
-                       best_p, flags, w, stream)))
-    return s;
-  CK(cudaEventRecord(p->ev_join, s2));
-  CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+  for (int k = np - 1; k >= 0; --k) {
+    const int b0 = (int)((long)B * k / np), b1 = (int)((long)B * (k + 1) / np);
+    cudaStream_t sk = k ? p->split_stream[k - 1] : st;
+    if (k) CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
+    const AlignWs wk = ws_at(*p, w, b0, tstride);
+    if ((s = align_range(plan, particles + vox * b0, tstride ? templates + vox * b0 : templates,
+                         b1 - b0, tstride, h_ready, P_per ? P_per + b0 : nullptr, euler + 3 * b0,
+                         R + 9 * b0, score + b0, best_p + b0, flags + b0, wk, sk)))
+      return s;
+    if (k) CK(cudaEventRecord(p->ev_join[k - 1], sk));
+  }
+  for (int k = 1; k < np; ++k) CK(cudaStreamWaitEvent(st, p->ev_join[k - 1], 0));
   return MATCHA_OK;
 }
 
