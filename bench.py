@@ -374,9 +374,13 @@ def main():
                flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
     H = plan.handle
     stages = ["analyze", "correlate", "soft", "newton", "select"]
-    # k_analyze2 x2 (particles, templates), k_correlate_deg, k_soft_chunk (grid and top-P
-    # fused), k_newton, k_final_select
-    KERNELS_PER_STEP = 6
+    # Kernels of one matcha_align step: per part of the batch k_analyze2 x2
+    # (particles, templates), the contraction, k_soft_chunk (grid and top-P
+    # fused), k_newton, k_final_select; from 256 particles on the batch runs as
+    # min(4, B / 128) concurrent parts (a shared template is analysed once).
+    parts = 1 if B < 256 else min(4, B // 128)
+    shared = temps.shape[0] != B
+    KERNELS_PER_STEP = parts * (5 if shared else 6) + (1 if shared else 0)
 
     def step(ev=None):
         def mark(i):
