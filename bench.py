@@ -70,8 +70,15 @@ def workload_config(w, B, ws):
         "particles_per_gpu": B, "box": w.N, "shells": w.n_shells, "L_final": w.L_final,
         "L0": w.L0, "K": w.K, "P": w.P, "M_iter": w.M_iter,
         "parallelism": "dp%d (particles sharded, no collective)" % ws,
-        "l2": "inputs %.1f GiB per step > 129 MB L2; no flush" % (2 * B * w.N ** 3 * 4 / 2 ** 30),
+        "l2": l2_note(2 * B * w.N ** 3 * 4),
     }
+
+
+def l2_note(nbytes):
+    """Whether a step's inputs exceed the GB300's 129 MB L2 (no flush needed)."""
+    if nbytes > 129e6:
+        return "inputs %.1f GiB per step > 129 MB L2; no flush" % (nbytes / 2 ** 30)
+    return "inputs %.0f MB per step, below the 129 MB L2" % (nbytes / 1e6)
 
 
 class ClockSampler:
