@@ -1,0 +1,36 @@
+"""Host-side helpers of bench.py: the per-kernel roofline arithmetic, the L2
+note, and the kernel count of a step (no GPU needed)."""
+import math
+
+import bench
+import paper_2603_15285_gb300 as m
+import synth
+
+
+def test_l2_note_compares_with_129_mb():
+    assert "> 129 MB L2" in bench.l2_note(2 * 1024 * 64 ** 3 * 4)
+    assert "below the 129 MB L2" in bench.l2_note(2 * 8 * 64 ** 3 * 4)
+
+
+def test_kernel_roofline_arithmetic():
+    w = synth.WORKLOADS["batch64"]
+    B = 1024
+    st = dict(analyze=2.0, correlate=0.5, soft=1.0, newton=2.0, select=0.01)
+    r = bench.kernel_roofline(w, B, m.FP32, st, 80.0, m)
+    peaks = bench.measured_peaks()
+    # analysis: particle + template volumes, 4 bytes per voxel, once each
+    want = 2 * 4 * 64 ** 3 * B / 2e-3 / 1e9
+    assert math.isclose(r["analysis"]["achieved"], want, rel_tol=1e-12)
+    assert math.isclose(r["analysis"]["frac"], want / peaks["hbm_gbs"], rel_tol=1e-12)
+    # contraction: 8 S T(L) flops per particle, T(32) = 47,905
+    T = 33 * 65 * 67 // 3
+    assert T == 47905
+    assert math.isclose(r["contraction"]["achieved"], 8.0 * 32 * T * B / 0.5e-3 / 1e12, rel_tol=1e-12)
+    assert math.isclose(r["contraction"]["frac"], r["contraction"]["achieved"] / 80.0, rel_tol=1e-12)
+    assert math.isclose(r["soft"]["grid_points_per_s"], 36 ** 3 * B / 1e-3, rel_tol=1e-12)
+    # tensor-core plans are measured against the tensor peak of their operand type
+    r16 = bench.kernel_roofline(w, B, m.BF16, st, 80.0, m)
+    r32 = bench.kernel_roofline(w, B, m.TF32, st, 80.0, m)
+    assert r16["contraction"]["bound"] == "tensor"
+    assert math.isclose(r32["contraction"]["peak"], r16["contraction"]["peak"] * 1.1 / 2.25,
+                        rel_tol=1e-12)
