@@ -385,7 +385,7 @@ def main():
     # (particles, templates), the contraction, k_soft_chunk (grid and top-P
     # fused), k_newton, k_final_select; from 256 particles on the batch runs as
     # min(4, B / 128) concurrent parts (a shared template is analysed once).
-    n_parts = 1 if B < 256 else min(4, B // 128)
+    n_parts = 1 if B < 256 else min(4, B // 128)  # (batch64's SOFFT is fused)
     shared = temps.shape[0] != B
     KERNELS_PER_STEP = n_parts * (5 if shared else 6) + (1 if shared else 0)
 

@@ -226,8 +226,9 @@ matcha_status matcha_final_select(matcha_plan plan, int B, const int *P_per_dev,
  * matcha_workspace_size(plan, B) bytes (256-byte aligned).  The call only
  * enqueues kernels on `stream` (no allocation, no synchronisation), so it can
  * be captured into a CUDA graph and replayed with the same buffers; the first
- * call on a plan should be made before capture.  From 256 particles on, the
- * batch runs as up to four concurrent parts, one on `stream` and the others
+ * call on a plan should be made before capture.  From 256 particles on (for
+ * plans whose SOFFT grid stays on chip), the batch runs as up to four
+ * concurrent parts, one on `stream` and the others
  * on streams the plan owns (forked from `stream` and joined back into it by
  * events), so the call's work stays ordered on `stream`; calls on one plan
  * from several host threads at once share those streams. */

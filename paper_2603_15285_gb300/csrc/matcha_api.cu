@@ -406,7 +406,9 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   size_t need = carve_align(*p, B, Bt, (char *)ws, &w);
   if (ws_bytes < need) return MATCHA_ERR_WORKSPACE;
   Range all("matcha_align");
-  if (B < 256)
+  // one pass for small batches, and where the SOFFT grid goes through HBM
+  // (large L0: its grid and scan kernels gain nothing from the split)
+  if (B < 256 || !soft_grid_optional(*p))
     return align_range(plan, particles, templates, B, tstride, false, P_per, euler, R, score,
                        best_p, flags, w, stream);
   // Parts of at least 128 particles on up to NSPLIT streams (the caller's and
