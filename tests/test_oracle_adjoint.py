@@ -129,3 +129,18 @@ def test_refined_score_gradient_matches_central_differences():
         assert abs(np.sum((np.conj(G[0]) * hv).real) - an[-1]) <= 1e-12 * np.abs(vox_grad).sum()
     fd, an = np.array(fd), np.array(an)
     assert np.max(np.abs(fd - an)) <= 1e-6 * np.max(np.abs(an)), (fd, an)
+
+
+def test_align_from_coefficients_equals_align_from_volumes():
+    """The coefficient-input entry of the oracle's Algorithm 1 is the volume
+    entry minus the analysis: same rotations and scores, bit for bit."""
+    w, parts, temps = _small_pair()
+    S, R, L = w.n_shells, w.N / 2 - 1, w.L_sched[-1]
+    kw = dict(S=S, r_max=R, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter, L_sched=list(w.L_sched))
+    ref = O.align_batch(parts, temps, **kw)
+    f = O.analyze_volume(parts[0], S, R, L)[None]
+    h = O.analyze_volume(temps[0], S, R, L)[None]
+    got = O.align_coefs_batch(f, h, N=w.N, **kw)
+    assert np.array_equal(got["euler"], ref["euler"])
+    assert np.array_equal(got["score"], ref["score"])
+    assert np.array_equal(got["best_p"], ref["best_p"])
