@@ -79,6 +79,21 @@ def test_null_handles_are_rejected(L):
     assert L.matcha_align(None, None, None, 1, 1, None, None, None, None, None, None, None, 0, None) == 1
 
 
+def test_newer_entry_points_check_arguments_on_the_host(L):
+    """The gradient, tuning and status calls reject missing handles and
+    outputs before any device work (status 1 = MATCHA_ERR_INVALID_ARG)."""
+    import ctypes
+    sz = ctypes.c_size_t(0)
+    bits = ctypes.c_int(0)
+    assert L.matcha_template_grad_workspace_size(None, 4, 0, ctypes.byref(sz)) == 1
+    assert L.matcha_template_grad(None, None, None, 4, 0, None, None, None, None, None, None,
+                                  None, 0, None) == 1
+    assert L.matcha_plan_autotune(None, None, None, 4, 1, None, 0, None, None) == 1
+    assert L.matcha_plan_device_status(None, ctypes.byref(bits)) == 1
+    assert L.matcha_plan_set_wait_limit(None, 0) == 1
+    assert L.matcha_host_workspace_size(None, 4, 1, ctypes.byref(sz)) == 1
+
+
 def test_layout_helper_counts_entries():
     for Lj in (8, 16, 32):
         rows = m.corr_layout(Lj)
