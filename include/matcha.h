@@ -70,7 +70,7 @@ typedef enum {
   MATCHA_ERR_INVALID_ARG = 1, /* bad pointer, size or descriptor field */
   MATCHA_ERR_CUDA = 2,        /* a CUDA call or kernel launch failed */
   MATCHA_ERR_WORKSPACE = 3,   /* workspace smaller than matcha_workspace_size */
-  MATCHA_ERR_TIMEOUT = 4,     /* reserved for bounded device-side waits */
+  MATCHA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (matcha_plan_device_status) */
   MATCHA_ERR_UNSUPPORTED = 5  /* valid but not implemented (e.g. a size limit) */
 } matcha_status;
 
@@ -90,10 +90,10 @@ typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1, MATCHA_TF32 = 2, MATCHA_BF16 = 
  *   precision    matcha_precision
  *   step_tol     Newton early stop (Section 2.4): a level stops for a candidate
  *                once ||delta||_2 < step_tol (radians); <= 0 selects 1e-9 for
- *                FP64 plans and 1e-6 for FP32 plans.
+ *                FP64 plans and 1e-6 for the 32-bit (FP32, TF32, BF16) plans.
  *   accept_tol   a Newton trial is accepted unless it lowers C_L by more than
  *                accept_tol |C_L|, the rounding level of the Wigner sums;
- *                <= 0 selects 1e-11 (FP64) or 1e-5 (FP32).
+ *                <= 0 selects 1e-11 (FP64) or 1e-5 (32-bit plans).
  * The angular sampling is n_theta = L_J + 1 Gauss-Legendre nodes in cos(theta)
  * and n_phi = 2 L_J + 2 equispaced phi per shell. */
 typedef struct {
@@ -118,7 +118,7 @@ typedef struct {
   long corr_entries;   /* (pair slot, l) entries per particle, empty slots included; 2 complex each */
   int n_pairs;         /* (L_J+1)^2 order pairs */
   int soft_n;          /* SOFFT points per angle, 2K(L0+1) */
-  int real_bytes;      /* 8 (FP64) or 4 (FP32) */
+  int real_bytes;      /* 8 (FP64) or 4 (FP32, TF32, BF16) */
 } matcha_plan_info_t;
 
 /* Builds the quadrature, Legendre, twiddle, Wigner-recurrence and SOFFT
