@@ -206,7 +206,10 @@ matcha_status matcha_soft_search_noalloc(matcha_plan plan, const void *c_dev, in
  * accepted trial.  work_dev (nullable) [B][2] receives, per particle, the
  * number of Wigner recurrence steps (one order pair, one degree, one
  * candidate) taken by evaluations with derivatives and by value-only trial
- * evaluations; it measures the work the march performed. */
+ * evaluations; it measures the work the march performed.  The 32-bit plans
+ * sum C, its gradient and Hessian in FP32 and solve the 3x3 Newton systems of
+ * the final level in FP64 (the earlier levels in FP32); angles, acceptance
+ * tests and scores are FP64 in every plan. */
 matcha_status matcha_newton_march(matcha_plan plan, const void *c_dev, int B,
                                   const int *n_cand_dev, double *euler_dev, double *score_dev,
                                   int *cand_flags_dev, long long *work_dev, void *stream);
