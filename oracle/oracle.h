@@ -52,6 +52,7 @@ void   orc_sample_shells(const float *vol, int N, int S, double R, int L, double
 void   orc_sh_analyze_shell(const double *samples, int L, double *coef);
 void   orc_sh_synthesize(const double *coef, int L, double theta, double phi, double *out);
 void   orc_analyze_volume(const float *vol, int N, int S, double R, int L, double *coef);
+void   orc_transform_volume(const float *vol, int N, const double *R, const double *s, float *out);
 
 /* ---- contraction (contraction.c) --------------------------------------- */
 void orc_correlate(const double *f, const double *h, int S, double R, int L, double *c);

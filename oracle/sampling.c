@@ -49,3 +49,24 @@ void orc_sample_shells(const float *vol, int N, int S, double R, int L, double *
       }
     }
 }
+
+/*
+ * Pose of a voxel volume (the appendix on alternating search over rotations
+ * and translations): out(x) = vol(R^T (x - c0) + c0 - s) at every voxel
+ * centre x, trilinear, zero outside, rounded to float32 like any volume.
+ * With R = I this is the translation (S_s vol)(x) = vol(x - s); with s = 0 it
+ * is the rotation g o vol about c0.  R is row-major; s = (x, y, z) voxels.
+ */
+void orc_transform_volume(const float *vol, int N, const double *R, const double *s, float *out) {
+  double c0 = 0.5 * N;
+  for (long k = 0; k < N; ++k)
+    for (long j = 0; j < N; ++j)
+      for (long i = 0; i < N; ++i) {
+        double x = i - c0, y = j - c0, z = k - c0;
+        /* R^T x: column c of R dotted with x */
+        double px = R[0] * x + R[3] * y + R[6] * z + c0 - s[0];
+        double py = R[1] * x + R[4] * y + R[7] * z + c0 - s[1];
+        double pz = R[2] * x + R[5] * y + R[8] * z + c0 - s[2];
+        out[(k * N + j) * N + i] = (float)orc_trilinear(vol, N, px, py, pz);
+      }
+}

@@ -12,9 +12,12 @@ Recipe (one particle = one (template, particle) pair, each from its own seed):
   ``U[0.5, 1]``;
 * ground truth rotation ``R*``: a normalised 4-vector of standard normals
   (a Haar-random unit quaternion);
-* clean particle ``s(x) = h(R*^T (x - c0) + c0)`` by trilinear interpolation of
-  the template (or, with ``exact_rotation=True``, the blobs re-rendered at the
-  rotated centres, which is the exact rotation of a sum of isotropic Gaussians);
+* clean particle ``s(x) = h(R*^T (x - c0) + c0 - tau*)`` by trilinear
+  interpolation of the template (or, with ``exact_rotation=True``, the blobs
+  re-rendered at the centres ``R* (c - c0 + tau*) + c0``, which is the exact
+  pose of a sum of isotropic Gaussians); the planted shift ``tau*`` is zero
+  unless the workload sets ``shift_max`` (then uniform in a ball of that radius,
+  in voxels), so that ``s = g* o S_tau* h`` with ``(S_tau h)(x) = h(x - tau)``;
 * noise: i.i.d. Gaussian with variance ``mean_box(s^2) / SNR``;
 * optional missing wedge (tilt axis y, beam z): keep the Fourier samples with
   ``|k_z| <= tan(wedge) * |k_x|`` plus the zero-frequency sample.
@@ -63,6 +66,9 @@ class Workload:
     snr_range: Optional[Tuple[float, float]] = None  # per-particle SNR ~ U[lo, hi] (overrides snr)
     P_range: Optional[Tuple[int, int]] = None        # per-particle candidate count ~ U{lo..hi}
     seed_offset: int = 0                             # index of particle 0 in the seed sequence
+    shift_max: float = 0.0                           # planted shift tau* uniform in this ball (voxels)
+    rounds: int = 1                                  # rotation-translation alternations (6-D pose)
+    max_shift: int = 0                               # integer shift search window, voxels per axis
 
     @property
     def r_max(self) -> float:
@@ -112,6 +118,16 @@ WORKLOADS = {
     "paper200": Workload("paper200", B=256, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,
                          snr=1.0, wedge_deg=60.0, n_shells=40, L_sched=(30, 40),
                          L0=30, K=2, P=10, M_iter=1, base_seed=20260321),
+    # 6-D pose (rotation and translation): planted shifts up to 3 voxels, three
+    # rotation-translation alternations, integer search window +-5 voxels.
+    "shift32": Workload("shift32", B=2, N=32, n_blobs=16, sigma=1.5, ball_radius=10.0,
+                        snr=0.5, wedge_deg=None, n_shells=12, L_sched=(8, 12, 16),
+                        L0=8, K=2, P=8, M_iter=3, base_seed=20260323, shift_max=2.5,
+                        rounds=3, max_shift=4),
+    "shift64": Workload("shift64", B=1024, N=64, n_blobs=48, sigma=2.0, ball_radius=24.0,
+                        snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 24, 32),
+                        L0=8, K=2, P=16, M_iter=3, base_seed=20260324, shift_max=3.0,
+                        rounds=3, max_shift=5),
 }
 
 
@@ -158,14 +174,16 @@ def render_blobs(N: int, offsets, amps, sigma: float, device="cpu") -> torch.Ten
     return v if batched else v[0]
 
 
-def rotate_trilinear(vol: torch.Tensor, R) -> torch.Tensor:
-    """out(x) = vol(R^T (x - c0) + c0) by trilinear interpolation, zero outside.
+def rotate_trilinear(vol: torch.Tensor, R, shift=None) -> torch.Tensor:
+    """out(x) = vol(R^T (x - c0) + c0 - shift) by trilinear interpolation, zero outside.
 
-    ``vol`` [N][N][N] with R [3][3], or batched [B][N][N][N] with R [B][3][3].
+    ``vol`` [N][N][N] with R [3][3] (shift [3] or None), or batched
+    [B][N][N][N] with R [B][3][3] (shift [B][3] or None).
     """
     batched = vol.dim() == 4
     if not batched:
         vol, R = vol[None], np.asarray(R)[None]
+        shift = None if shift is None else np.asarray(shift)[None]
     Bn, N = vol.shape[0], vol.shape[-1]
     dev = vol.device
     c0 = N / 2
@@ -174,6 +192,8 @@ def rotate_trilinear(vol: torch.Tensor, R) -> torch.Tensor:
     zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
     x = torch.stack([xx, yy, zz], -1).reshape(-1, 3)                          # [V][3]
     pts = torch.einsum("vj,bij->bvi", x, Rt.transpose(1, 2)) + c0             # R^T x + c0
+    if shift is not None:
+        pts = pts - torch.as_tensor(np.asarray(shift), dtype=torch.float64, device=dev)[:, None, :]
     i0 = torch.floor(pts).long()
     fr = pts - i0
     out = torch.zeros(pts.shape[:2], dtype=vol.dtype, device=dev)
@@ -211,7 +231,8 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
 
     Returns dict with ``templates`` (float32 [Bt][N][N][N], Bt = 1 when the
     workload shares one template, else B), ``particles`` (float32 [B][N][N][N]),
-    ``R_true`` (float64 [B][3][3]).  Random draws are made per particle on the
+    ``R_true`` (float64 [B][3][3]), ``tau_true`` (float64 [B][3], (x, y, z)
+    voxels; zero unless the workload plants shifts).  Random draws are made per particle on the
     host; rendering runs in chunks of ``chunk`` particles on ``device``.
     """
     B = w.B if B is None else B
@@ -221,6 +242,7 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
     parts = torch.empty((B, N, N, N), dtype=torch.float32, device=device)
     temps = None if w.shared_template else torch.empty((B, N, N, N), dtype=torch.float32, device=device)
     Rs = np.empty((B, 3, 3))
+    taus = np.zeros((B, 3))
     snrs = np.full(B, w.snr if w.snr is not None else 0.0)
     P_per = np.full(B, w.P, dtype=np.int32)
     shared = None
@@ -244,19 +266,27 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
                 snrs[b] = rng.uniform(*w.snr_range)
             if w.P_range is not None:
                 P_per[b] = rng.integers(w.P_range[0], w.P_range[1] + 1)
+            if w.shift_max > 0:
+                while True:
+                    t = rng.uniform(-w.shift_max, w.shift_max, size=3)
+                    if t @ t <= w.shift_max * w.shift_max:
+                        break
+                taus[b] = t
             if noise and snrs[b] > 0:
                 etas.append(rng.standard_normal((N, N, N), dtype=np.float32))
         Rc = Rs[c0:c0 + len(idx)]
+        tc = taus[c0:c0 + len(idx)] if w.shift_max > 0 else None
         if shared is None:
             h = render_blobs(N, np.stack(offs_l), np.stack(amps_l), w.sigma, device)
             temps[c0:c0 + len(idx)] = h.float()
         else:
             h = shared[2][None].expand(len(idx), N, N, N)
         if exact_rotation:
-            rot = np.einsum("bnj,bij->bni", np.stack(offs_l), Rc)
+            o = np.stack(offs_l) + (0.0 if tc is None else tc[:, None, :])
+            rot = np.einsum("bnj,bij->bni", o, Rc)
             s = render_blobs(N, rot, np.stack(amps_l), w.sigma, device)
         else:
-            s = rotate_trilinear(h.contiguous(), Rc)
+            s = rotate_trilinear(h.contiguous(), Rc, tc)
         if etas:
             snr = torch.as_tensor(snrs[c0:c0 + len(idx)], dtype=s.dtype, device=device)
             var = (s * s).mean(dim=(1, 2, 3)) / snr
@@ -269,6 +299,7 @@ def make_batch(w: Workload, B: Optional[int] = None, start: int = 0, device="cpu
         "templates": temps,
         "particles": parts,
         "R_true": Rs,
+        "tau_true": taus,
         "snr": snrs,
         "P_per": P_per,
     }
