@@ -94,6 +94,9 @@ typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1, MATCHA_TF32 = 2, MATCHA_BF16 = 
  *   accept_tol   a Newton trial is accepted unless it lowers C_L by more than
  *                accept_tol |C_L|, the rounding level of the Wigner sums;
  *                <= 0 selects 1e-11 (FP64) or 1e-5 (32-bit plans).
+ *   refine       0: Newton steps (Section 2.2); 1: gradient steps
+ *                delta = grad / ||H||_F with the same clamp and step control,
+ *                the first-order method Section 5.1 compares against.
  * The angular sampling is n_theta = L_J + 1 Gauss-Legendre nodes in cos(theta)
  * and n_phi = 2 L_J + 2 equispaced phi per shell. */
 typedef struct {
@@ -109,6 +112,7 @@ typedef struct {
   int precision;
   double step_tol;
   double accept_tol;
+  int refine;
 } matcha_plan_desc;
 
 /* Sizes derived from a plan. */
@@ -180,19 +184,22 @@ matcha_status matcha_soft_search(matcha_plan plan, const void *c_dev, int B, con
  * owned by a single allocator (a framework's caching allocator or a pool sized
  * at start-up) and latency-critical loops that cannot afford cudaMalloc and
  * cudaFree, which may synchronise the device.  The caller passes c and the
- * candidate outputs exactly as for matcha_soft_search; the SOFFT grid lives in
- * a fixed array of MATCHA_NOALLOC_GRID_BYTES (64 MiB) compiled into the
- * library, which every GPU that loads the library keeps until the process
- * exits.  B * soft_n^3 * real_bytes must fit in it (for the 1024-particle
- * 64^3 plan with L0 = 8, K = 2: 359 particles per call in FP32, 179 in
- * FP64); larger batches return MATCHA_ERR_UNSUPPORTED with the limit in
- * matcha_last_error().  The call allocates nothing.  Its first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current) and caches it; make that first call before any stream
- * capture.  All calls on a device share the array: calls that overlap on the
- * GPU (e.g. on different streams) race on it and must be ordered by the
- * caller.  The grid is fully rewritten on each call, so leftover contents of
- * the previous call do not matter. */
+ * candidate outputs exactly as for matcha_soft_search.  Plans whose SOFFT
+ * grid fits the fused on-chip kernels (e.g. L0 = 8, K = 2) need no grid
+ * scratch at all and take batches up to 65535, as matcha_soft_search.  Plans
+ * whose grid goes through memory (e.g. L0 = 30, K = 2: 124^3 points per
+ * particle) keep it in a fixed array of MATCHA_NOALLOC_GRID_BYTES (64 MiB)
+ * compiled into the library, which every GPU that loads the library keeps
+ * until the process exits; for them B * soft_n^3 * real_bytes must fit in it
+ * (8 particles per call in FP32, 4 in FP64 at L0 = 30, K = 2), and larger
+ * batches return MATCHA_ERR_UNSUPPORTED with the limit in
+ * matcha_last_error().  The call allocates nothing.  For such a plan its
+ * first call looks up the array's device address (cudaGetSymbolAddress, with
+ * the plan's device current) and keeps it in the plan; make that first call
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU (e.g. on different streams) race on it and must be
+ * ordered by the caller.  The grid is fully rewritten on each call, so
+ * leftover contents of the previous call do not matter. */
 #define MATCHA_NOALLOC_GRID_BYTES (64u << 20)
 matcha_status matcha_soft_search_noalloc(matcha_plan plan, const void *c_dev, int B,
                                          const int *P_per_dev, int *idx_dev, double *euler_dev,
@@ -315,6 +322,63 @@ matcha_status matcha_template_grad(matcha_plan plan, const void *f_dev, const vo
                                    const double *weight_dev, void *coef_grad_dev,
                                    double *vox_grad_dev, double *shift_dev, int *flags_dev,
                                    void *ws_dev, size_t ws_bytes, void *stream);
+
+/* 6-D pose: rotation and translation (the appendix "Alternating search over
+ * rotations and translations"; T = 3 alternations in Section 5.2).
+ *
+ * The objective is C(tau, g) = <f, g o S_tau h>, (S_tau h)(x) = h(x - tau).
+ * At a fixed g it is the cross-correlation CC(t) = sum_x f(x) u(x - t) of f
+ * and the rotated template u = g o h at t = g tau (so tau = R^T t).  CC is
+ * the circular correlation a 3-D FFT computes (indices mod N); it is
+ * searched on the integer window t in [-max_shift, max_shift]^3, then
+ * refined on a grid of 2 floor(0.75 upsample) + 1 points per axis at spacing
+ * 1/upsample around the integer peak, where CC is the trigonometric
+ * interpolant N^-3 Re sum_k X(k) e^{2 pi i k.t/N}, X = F conj(U), k in
+ * [-N/2, N/2)^3 (the upsampled DFT the paper cites for sub-voxel accuracy).
+ * Grid maxima: ties to the smaller [z][y][x] index.  Vectors t, tau are
+ * (x, y, z) in voxels.  The box edge N must factor into 2, 3 and 5
+ * (MATCHA_ERR_UNSUPPORTED otherwise); 0 <= max_shift <= 64 with
+ * 2 max_shift + 1 <= N, 1 <= upsample <= 64.  Plan precision: FP64 plans run
+ * the FFT and the correlation in FP64, the 32-bit plans in FP32.
+ *
+ * matcha_transform_volumes: out_b(x) = vol(R_b^T (x - c0) + c0 - shift_b),
+ *   trilinear, zero outside, for B volumes (vol_stride 0: one shared input
+ *   volume, 1: one per output); R_dev [B][9] row-major and shift_dev [B][3]
+ *   are nullable (identity, zero).  precision MATCHA_FP64 interpolates in
+ *   FP64, the others in FP32.  With R = I this is the translation S_shift,
+ *   with shift = 0 the rotation g o vol about c0. */
+matcha_status matcha_transform_volumes(int N, const float *vols_dev, int B, int vol_stride,
+                                       const double *R_dev, const double *shift_dev, int precision,
+                                       float *out_dev, void *stream);
+/* matcha_shift_search: the translation search of particle b against the
+ * already rotated template rotated_dev[b] (B volumes each).  Outputs t_dev
+ * [B][3], cc_dev [B] (CC at t), flags_dev [B] (set to 32 when the integer
+ * peak lies on the window's edge, i.e. the true shift may lie beyond it);
+ * with R_dev [B][9] given, tau_dev [B][3] = R^T t (both nullable together).
+ * ws_dev: matcha_shift_search_workspace_size bytes, 256-byte aligned. */
+matcha_status matcha_shift_search_workspace_size(matcha_plan plan, int B, int max_shift,
+                                                 int upsample, size_t *bytes);
+matcha_status matcha_shift_search(matcha_plan plan, const float *particles_dev,
+                                  const float *rotated_dev, int B, int max_shift, int upsample,
+                                  const double *R_dev, double *t_dev, double *tau_dev,
+                                  double *cc_dev, int *flags_dev, void *ws_dev, size_t ws_bytes,
+                                  void *stream);
+/* matcha_align6d: `rounds` alternations starting from tau = 0; round r runs
+ * matcha_align on (f, S_tau h) (the template itself in round 0), then
+ * matcha_shift_search on u = g o h and sets tau = R^T t.  Outputs the last
+ * round's euler [B][3], R [B][9], score [B] (C_{L_J} of the rotation step),
+ * tau [B][3], t [B][3], cc [B] and flags [B] (matcha_align's bits, plus 32
+ * from the last translation search).  ws_dev: matcha_align6d_workspace_size
+ * bytes (it contains matcha_align's workspace), 256-byte aligned.  Only
+ * enqueues work on `stream`. */
+matcha_status matcha_align6d_workspace_size(matcha_plan plan, int B, int template_batch_stride,
+                                            int max_shift, int upsample, size_t *bytes);
+matcha_status matcha_align6d(matcha_plan plan, const float *particles_dev,
+                             const float *templates_dev, int B, int template_batch_stride,
+                             int rounds, int max_shift, int upsample, double *euler_dev,
+                             double *R_dev, double *tau_dev, double *t_dev, double *score_dev,
+                             double *cc_dev, int *flags_dev, void *ws_dev, size_t ws_bytes,
+                             void *stream);
 
 const char *matcha_status_string(matcha_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */

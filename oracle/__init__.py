@@ -27,7 +27,7 @@ class OrcParams(ctypes.Structure):
                 ("K", ctypes.c_int), ("P", ctypes.c_int), ("M_iter", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("L_sched", ctypes.c_int * 16),
                 ("r_max", ctypes.c_double), ("step_tol", ctypes.c_double),
-                ("accept_tol", ctypes.c_double)]
+                ("accept_tol", ctypes.c_double), ("refine", ctypes.c_int)]
 
 
 def lib():
@@ -256,14 +256,23 @@ def newton_direction(g, H, L):
     return d, fl
 
 
-def newton_march(c, L_sched, M_iter, abg, step_tol=1e-9, accept_tol=1e-11):
+def newton_march(c, L_sched, M_iter, abg, step_tol=1e-9, accept_tol=1e-11, method=0):
+    """method 0: Newton steps; 1: gradient steps."""
     ca = _split(np.asarray(c))
     Ls = np.ascontiguousarray(L_sched, dtype=np.int32)
     x = np.array(abg, dtype=np.float64)
     sc = np.zeros(1)
-    fl = lib().orc_newton_march(_d(ca), _i(Ls), ctypes.c_int(len(Ls)), ctypes.c_int(M_iter),
-                                ctypes.c_double(step_tol), ctypes.c_double(accept_tol), _d(x), _d(sc))
+    fl = lib().orc_refine_march(_d(ca), _i(Ls), ctypes.c_int(len(Ls)), ctypes.c_int(M_iter),
+                                ctypes.c_double(step_tol), ctypes.c_double(accept_tol),
+                                ctypes.c_int(method), _d(x), _d(sc))
     return x, sc[0], fl
+
+
+def gradient_direction(g, H, L):
+    ga = np.ascontiguousarray(g, dtype=np.float64); Ha = np.ascontiguousarray(H, dtype=np.float64).reshape(9)
+    d = np.zeros(3)
+    lib().orc_gradient_direction(_d(ga), _d(Ha), ctypes.c_int(L), _d(d))
+    return d
 
 
 # ---- full path ----------------------------------------------------------------
@@ -271,8 +280,10 @@ def max_threads():
     return lib().orc_max_threads()
 
 
-def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9, accept_tol=1e-11):
+def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9, accept_tol=1e-11,
+                refine=0):
     p = OrcParams()
+    p.refine = refine
     p.N, p.S, p.L0, p.K, p.P, p.M_iter = N, S, L0, K, P, M_iter
     p.n_levels = len(L_sched)
     for i, L in enumerate(L_sched):
@@ -284,16 +295,17 @@ def make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol=1e-9, accept_to
 
 
 def align_batch(particles, templates, *, S, r_max, L0, K, P, M_iter, L_sched,
-                P_per=None, n_threads=0, step_tol=1e-9, accept_tol=1e-11):
+                P_per=None, n_threads=0, step_tol=1e-9, accept_tol=1e-11, refine=0):
     """Run Algorithm 1 on each (particle, template) pair; returns a dict of arrays.
 
-    ``templates`` holds one volume per particle, or a single shared volume.
+    ``templates`` holds one volume per particle, or a single shared volume;
+    ``refine`` 1 replaces the Newton steps by gradient steps.
     """
     parts = np.ascontiguousarray(particles, dtype=np.float32)
     temps = np.ascontiguousarray(templates, dtype=np.float32)
     B, N = parts.shape[0], parts.shape[-1]
     tstride = 0 if temps.shape[0] == 1 else N ** 3
-    p = make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol, accept_tol)
+    p = make_params(N, S, r_max, L0, K, P, M_iter, L_sched, step_tol, accept_tol, refine)
     out = dict(euler=np.zeros((B, 3)), R=np.zeros((B, 3, 3)), score=np.zeros(B),
                best_p=np.zeros(B, dtype=np.int32), flags=np.zeros(B, dtype=np.int32),
                cand_idx=np.full((B, P), -1, dtype=np.int32), cand_euler0=np.zeros((B, P, 3)),

@@ -52,7 +52,7 @@ int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, i
     orc_soft_angles(n, idx[q], abg);
     if (cand_euler0) memcpy(cand_euler0 + 3 * q, abg, sizeof(abg));
     double s;
-    fl |= orc_newton_march(c, p->L_sched, p->n_levels, p->M_iter, p->step_tol, p->accept_tol, abg, &s);
+    fl |= orc_refine_march(c, p->L_sched, p->n_levels, p->M_iter, p->step_tol, p->accept_tol, p->refine, abg, &s);
     if (cand_idx) cand_idx[q] = idx[q];
     if (cand_euler) memcpy(cand_euler + 3 * q, abg, sizeof(abg));
     if (cand_score) cand_score[q] = s;
@@ -68,7 +68,7 @@ int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, i
     else {
       orc_soft_angles(n, idx[best], abg);
       double s;
-      orc_newton_march(c, p->L_sched, p->n_levels, p->M_iter, p->step_tol, p->accept_tol, abg, &s);
+      orc_refine_march(c, p->L_sched, p->n_levels, p->M_iter, p->step_tol, p->accept_tol, p->refine, abg, &s);
     }
     memcpy(euler, abg, sizeof(abg));
     orc_euler_to_matrix(abg[0], abg[1], abg[2], R);

@@ -85,6 +85,21 @@ int orc_newton_direction(const double *g, const double *H, int L, double *delta)
   return flags;
 }
 
+/* First-order alternative (Section 5.1 compares Newton refinement with a
+ * gradient method): delta = grad / ||H||_F, the gradient step with the
+ * inverse of a local curvature bound as step size (||H||_2 <= ||H||_F), then
+ * the same clamp.  No flag: this direction is the method, not a fallback. */
+int orc_gradient_direction(const double *g, const double *H, int L, double *delta) {
+  double hn = 0.0;
+  for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
+  hn = sqrt(hn);
+  for (int i = 0; i < 3; ++i) delta[i] = hn > 0 ? g[i] / hn : 0.0;
+  double nrm = sqrt(delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2]);
+  double cap = M_PI / (2.0 * (L + 1.0));
+  if (nrm > cap) for (int i = 0; i < 3; ++i) delta[i] *= cap / nrm;
+  return 0;
+}
+
 static int finite_all(double C, const double *g, const double *H) {
   if (!isfinite(C)) return 0;
   for (int i = 0; i < 3; ++i) if (!isfinite(g[i])) return 0;
@@ -92,10 +107,17 @@ static int finite_all(double C, const double *g, const double *H) {
   return 1;
 }
 
-/* Refines abg in place through the schedule; *score = C_{L_J}(abg).
- * Returns flag bits. */
 int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_iter,
                      double step_tol, double accept_tol, double *abg, double *score) {
+  return orc_refine_march(c, L_sched, n_levels, M_iter, step_tol, accept_tol, 0, abg, score);
+}
+
+/* Refines abg in place through the schedule; *score = C_{L_J}(abg).
+ * method 0: Newton steps, 1: gradient steps (orc_gradient_direction); the
+ * step control is the same.  Returns flag bits. */
+int orc_refine_march(const double *c, const int *L_sched, int n_levels, int M_iter,
+                     double step_tol, double accept_tol, int method, double *abg,
+                     double *score) {
   int flags = 0;
   double C = NAN;
   for (int lev = 0; lev < n_levels; ++lev) {
@@ -104,7 +126,8 @@ int orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_it
       double g[3], H[9], delta[3];
       C = orc_objective(c, L, abg[0], abg[1], abg[2], g, H, NULL);
       if (!finite_all(C, g, H)) { *score = C; return flags | 1; }
-      flags |= orc_newton_direction(g, H, L, delta);
+      flags |= method == 1 ? orc_gradient_direction(g, H, L, delta)
+                           : orc_newton_direction(g, H, L, delta);
       if (sqrt(delta[0] * delta[0] + delta[1] * delta[1] + delta[2] * delta[2]) < step_tol) break;
       int accepted = 0;
       for (int h = 0; h < 3 && !accepted; ++h) {

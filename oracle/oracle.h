@@ -80,6 +80,10 @@ void orc_wrap(double *abg);
 int  orc_newton_direction(const double *g, const double *H, int L, double *delta);
 int  orc_newton_march(const double *c, const int *L_sched, int n_levels, int M_iter,
                       double step_tol, double accept_tol, double *abg, double *score);
+int  orc_gradient_direction(const double *g, const double *H, int L, double *delta);
+int  orc_refine_march(const double *c, const int *L_sched, int n_levels, int M_iter,
+                      double step_tol, double accept_tol, int method, double *abg,
+                      double *score);
 
 /* ---- full path (align.c) ------------------------------------------------ */
 typedef struct {
@@ -88,6 +92,7 @@ typedef struct {
   double r_max;
   double step_tol;
   double accept_tol;
+  int refine;               /* 0 Newton steps, 1 gradient steps */
 } orc_params;
 
 int orc_align_one(const orc_params *p, const float *particle, const float *tmpl, int P_this,

@@ -30,6 +30,8 @@ SYMBOLS = [
     "matcha_align_host", "matcha_status_string", "matcha_last_error",
     "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
     "matcha_plan_device_status", "matcha_plan_autotune", "matcha_plan_set_wait_limit",
+    "matcha_transform_volumes", "matcha_shift_search_workspace_size", "matcha_shift_search",
+    "matcha_align6d_workspace_size", "matcha_align6d",
 ]
 
 
@@ -42,7 +44,8 @@ class PlanDesc(ctypes.Structure):
                 ("L0", ctypes.c_int), ("K_oversample", ctypes.c_int), ("P_max", ctypes.c_int),
                 ("M_iter", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("L_sched", ctypes.c_int * MATCHA_MAX_LEVELS), ("precision", ctypes.c_int),
-                ("step_tol", ctypes.c_double), ("accept_tol", ctypes.c_double)]
+                ("step_tol", ctypes.c_double), ("accept_tol", ctypes.c_double),
+                ("refine", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -88,6 +91,12 @@ def lib():
             "matcha_plan_set_wait_limit": [_vp, l],
             "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
+            "matcha_transform_volumes": [i, _vp, i, i, _vp, _vp, i, _vp, _vp],
+            "matcha_shift_search_workspace_size": [_vp, i, i, i, ctypes.POINTER(sz)],
+            "matcha_shift_search": [_vp, _vp, _vp, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
+            "matcha_align6d_workspace_size": [_vp, i, i, i, i, ctypes.POINTER(sz)],
+            "matcha_align6d": [_vp, _vp, _vp, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                               _vp, sz, _vp],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -129,7 +138,7 @@ class Plan:
 
     def __init__(self, box_n: int, n_shells: int, L0: int, K: int, P: int, M_iter: int,
                  L_sched: Sequence[int], precision: int = FP64, r_max: float = 0.0,
-                 step_tol: float = 0.0, accept_tol: float = 0.0):
+                 step_tol: float = 0.0, accept_tol: float = 0.0, refine: int = 0):
         _torch()
         d = PlanDesc()
         d.box_n, d.n_shells, d.r_max = box_n, n_shells, r_max
@@ -140,6 +149,7 @@ class Plan:
         for k, L in enumerate(L_sched):
             d.L_sched[k] = int(L)
         d.precision, d.step_tol, d.accept_tol = precision, step_tol, accept_tol
+        d.refine = refine
         h = _vp()
         _check(lib().matcha_plan_create(ctypes.byref(d), ctypes.byref(h)), "matcha_plan_create")
         self._h = h
@@ -347,6 +357,88 @@ def matcha_align(plan: Plan, particles, templates, P_per=None, ws=None, out=None
                               _ptr(out["euler"]), _ptr(out["R"]), _ptr(out["score"]),
                               _ptr(out["best_p"]), _ptr(out["flags"]), aligned, nbytes, _stream()),
            "matcha_align")
+    return out
+
+
+def _aligned(ws):
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    return aligned, ws.numel() - (aligned - base)
+
+
+def matcha_transform_volumes(vols, R=None, shift=None, B=None, precision: int = FP64, out=None):
+    """out_b(x) = vol(R_b^T (x - c0) + c0 - shift_b), trilinear (a shared input
+    volume when ``vols`` holds one and B > 1)."""
+    torch = _torch()
+    _need(vols, torch.float32, "vols")
+    N = vols.shape[-1]
+    B = vols.shape[0] if B is None else B
+    stride = 0 if vols.shape[0] == 1 and B != 1 else 1
+    if R is not None:
+        _need(R, torch.float64, "R")
+    if shift is not None:
+        _need(shift, torch.float64, "shift")
+    if out is None:
+        out = torch.empty((B, N, N, N), dtype=torch.float32, device="cuda")
+    _check(lib().matcha_transform_volumes(N, _ptr(vols), B, stride, _ptr(R), _ptr(shift), precision,
+                                          _ptr(out), _stream()), "matcha_transform_volumes")
+    return out
+
+
+def matcha_shift_search(plan: Plan, particles, rotated, max_shift: int, upsample: int, R=None,
+                        ws=None):
+    """Translation of each particle against its rotated template (t, tau = R^T t, cc, flags)."""
+    torch = _torch()
+    _need(particles, torch.float32, "particles"); _need(rotated, torch.float32, "rotated")
+    B = particles.shape[0]
+    if R is not None:
+        _need(R, torch.float64, "R")
+    if ws is None:
+        n = ctypes.c_size_t()
+        _check(lib().matcha_shift_search_workspace_size(plan.handle, B, max_shift, upsample,
+                                                        ctypes.byref(n)), "workspace size")
+        ws = torch.empty((n.value + 256,), dtype=torch.uint8, device="cuda")
+    out = dict(t=torch.empty((B, 3), dtype=torch.float64, device="cuda"),
+               tau=torch.empty((B, 3), dtype=torch.float64, device="cuda") if R is not None else None,
+               cc=torch.empty((B,), dtype=torch.float64, device="cuda"),
+               flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
+    a, nb = _aligned(ws)
+    _check(lib().matcha_shift_search(plan.handle, _ptr(particles), _ptr(rotated), B, max_shift,
+                                     upsample, _ptr(R), _ptr(out["t"]), _ptr(out["tau"]),
+                                     _ptr(out["cc"]), _ptr(out["flags"]), a, nb, _stream()),
+           "matcha_shift_search")
+    return out
+
+
+def alloc_workspace6d(plan: Plan, B: int, stride: int, max_shift: int, upsample: int):
+    torch = _torch()
+    n = ctypes.c_size_t()
+    _check(lib().matcha_align6d_workspace_size(plan.handle, B, stride, max_shift, upsample,
+                                               ctypes.byref(n)), "workspace size")
+    return torch.empty((n.value + 256,), dtype=torch.uint8, device="cuda")
+
+
+def matcha_align6d(plan: Plan, particles, templates, rounds: int, max_shift: int, upsample: int,
+                   ws=None, out=None):
+    """6-D pose by ``rounds`` rotation-translation alternations (device tensors)."""
+    torch = _torch()
+    _need(particles, torch.float32, "particles"); _need(templates, torch.float32, "templates")
+    B = particles.shape[0]
+    stride = 0 if templates.shape[0] == 1 and B != 1 else 1
+    if ws is None:
+        ws = alloc_workspace6d(plan, B, stride, max_shift, upsample)
+    if out is None:
+        f64 = dict(dtype=torch.float64, device="cuda")
+        out = dict(euler=torch.empty((B, 3), **f64), R=torch.empty((B, 3, 3), **f64),
+                   tau=torch.empty((B, 3), **f64), t=torch.empty((B, 3), **f64),
+                   score=torch.empty((B,), **f64), cc=torch.empty((B,), **f64),
+                   flags=torch.empty((B,), dtype=torch.int32, device="cuda"))
+    a, nb = _aligned(ws)
+    _check(lib().matcha_align6d(plan.handle, _ptr(particles), _ptr(templates), B, stride, rounds,
+                                max_shift, upsample, _ptr(out["euler"]), _ptr(out["R"]),
+                                _ptr(out["tau"]), _ptr(out["t"]), _ptr(out["score"]),
+                                _ptr(out["cc"]), _ptr(out["flags"]), a, nb, _stream()),
+           "matcha_align6d")
     return out
 
 

@@ -12,8 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "_lib", "libmatcha.so")
+PROBE = os.path.join(HERE, "_lib", "libpeakprobe.so")
 SOURCES = ["matcha_api.cu", "plan_tables.cu", "analyze.cu", "correlate.cu", "soft.cu", "newton.cu",
-           "noalloc.cu", "backward.cu",
+           "noalloc.cu", "backward.cu", "translate.cu", "pose6d.cu",
            "correlate_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -63,6 +64,11 @@ def build(force=False, verbose=False, ptxas_v=False):
         tmp = OUT + ".tmp%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
         os.replace(tmp, OUT)
+    # the FP32 throughput probe the bench divides ALU work by (not part of the path)
+    probe_src = os.path.join(CSRC, "peak_probe.cu")
+    if force or _stale(PROBE, [probe_src]):
+        run([nvcc] + ARCH + FLAGS + ["-shared", "-o", PROBE + ".tmp", probe_src])
+        os.replace(PROBE + ".tmp", PROBE)
     # a C program using the library through its C ABI alone
     ex_src = os.path.join(HERE, "examples", "align_from_c.c")
     ex_out = os.path.join(HERE, "_lib", "align_from_c")

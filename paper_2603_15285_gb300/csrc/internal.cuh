@@ -14,8 +14,11 @@ struct Plan {
   int Ls[MATCHA_MAX_LEVELS];
   double R, step_tol, accept_tol;
   bool fp64;
+  int refine;    // 0 Newton steps, 1 gradient steps
   int tc;        // contraction on the tensor cores: 0 no, 1 TF32, 2 BF16 (FP32 plans)
   int *dev_err;  // device word: bit 0 = a tensor-core wait reached its limit
+  int device = -1;                 // the CUDA device current at plan creation
+  void *noalloc_grid = nullptr;    // device address of the allocation-free search's array
   // tile choices set by matcha_plan_autotune (0 = the built-in rule); none of
   // them changes any result bit
   int tune_shells = 0;   // shells per analysis CTA (1, 2, 4, 8)
@@ -38,6 +41,9 @@ struct Plan {
   int Mp;                       // orders padded to a multiple of 4
   int Qf, Mq;                   // folded DFT rows ceil(L_J/2); columns per order parity, padded to 4
   void *ring;                   // real [S * nt][2]: (r_s sin t_j, N/2 + r_s cos t_j) of ring s * nt + j
+  void *fft_tw;                 // real [N][2]: cos, sin (-2 pi j / N), the box FFT's twiddles
+  int fft_npass = 0;            // radix passes of the length-N FFT (0: N has a factor > 5)
+  int fft_radix[16] = {};       // radices (4, 2, 3, 5) in pass order
   int *pair_base;               // [npairs] first real of pair q in the grouped L_J layout
   int *pair_off0;               // [npairs0] entry offset of pair q in the L0 (SOFFT) layout
   // copy stream and events of matcha_align_host (created on first use)
@@ -108,6 +114,22 @@ bool backward_fits(const Plan &p);  // the template-gradient kernel's shared mem
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 bool analyze_shells_ok(const Plan &p, int G);  // G shells per analysis CTA fit
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
+// Translation search (translate.cu): volume poses, the box FFT, the cross
+// spectrum and the windowed inverse DFT of the correlation.
+cudaError_t launch_pose_volumes(int N, const float *vol, int B, long vol_stride, const double *R,
+                                const double *shift, bool fp64, float *out, cudaStream_t st);
+struct ShiftWs {
+  void *Z;        // complex [B][N^3] (plan precision): spectra, then the cross spectrum
+  void *Y1, *Y2;  // complex [B][nt][N^2], [B][nt][nt][N]
+  void *E;        // complex [B][3][N][nt]: the inverse-DFT factors per axis
+  void *CC;       // real [B][nt^3]
+  double *t0;     // [B][3] integer peak
+};
+size_t shift_ws_bytes(const Plan &p, int B, int max_shift, int upsample, char *base, ShiftWs *w);
+template <typename T>
+cudaError_t launch_shift_search(const Plan &p, const float *f, const float *u, int B,
+                                int max_shift, int upsample, const double *R, const ShiftWs &w,
+                                double *t, double *tau, double *cc, int *flags, cudaStream_t st);
 cudaError_t launch_final_select(const Plan &p, int B, const int *P_per, const int *n_cand,
                                 const double *cand_euler, const double *cand_score,
                                 const int *cand_flags, double *euler, double *R, double *score,

@@ -109,6 +109,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   if (d->precision < MATCHA_FP64 || d->precision > MATCHA_BF16) return MATCHA_ERR_INVALID_ARG;
   if (!isfinite(d->r_max) || !isfinite(d->step_tol) || !isfinite(d->accept_tol))
     return MATCHA_ERR_INVALID_ARG;
+  if (d->refine != 0 && d->refine != 1) return MATCHA_ERR_INVALID_ARG;
 
   Plan *p = new Plan();
   p->desc = *d;
@@ -118,6 +119,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->LJ = d->L_sched[d->n_levels - 1];
   p->R = d->r_max > 0 ? d->r_max : 0.5 * d->box_n - 1.0;
   p->fp64 = d->precision == MATCHA_FP64;
+  p->refine = d->refine;
   p->tc = d->precision == MATCHA_TF32 ? 1 : d->precision == MATCHA_BF16 ? 2 : 0;
   p->step_tol = d->step_tol > 0 ? d->step_tol : (p->fp64 ? 1e-9 : 1e-6);
   p->accept_tol = d->accept_tol > 0 ? d->accept_tol : (p->fp64 ? 1e-11 : 1e-5);
@@ -168,7 +170,10 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_dcs = add(rs * 4 * (size_t)p->Qf * p->Mq);
   size_t o_ring = add(rs * 2 * (size_t)p->S * p->nt);
   size_t o_err = add(sizeof(int));
-  cudaError_t e = cudaMalloc(&p->base, sz);
+  size_t o_fft = add(rs * 2 * (size_t)p->N);
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaGetDevice"); }
+  e = cudaMalloc(&p->base, sz);
   if (e != cudaSuccess) { delete p; return fail_cuda(e, "cudaMalloc(plan tables)"); }
   char *b = (char *)p->base;
   p->rs = (double *)(b + o_rs); p->wrad = (double *)(b + o_w);
@@ -179,7 +184,25 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->dft_cs = b + o_dcs;
   p->ring = b + o_ring;
   p->dev_err = (int *)(b + o_err);
+  p->fft_tw = b + o_fft;
+  {  // radices of the box FFT (translation search): 4s first, then 2, 3, 5
+    int n = p->N, np = 0;
+    while (n % 4 == 0 && np < 16) { p->fft_radix[np++] = 4; n /= 4; }
+    while (n % 2 == 0 && np < 16) { p->fft_radix[np++] = 2; n /= 2; }
+    while (n % 3 == 0 && np < 16) { p->fft_radix[np++] = 3; n /= 3; }
+    while (n % 5 == 0 && np < 16) { p->fft_radix[np++] = 5; n /= 5; }
+    p->fft_npass = n == 1 ? np : 0;
+  }
+  std::vector<double> tw(2 * (size_t)p->N);
+  for (int j = 0; j < p->N; ++j) {
+    tw[2 * j] = cos(2.0 * M_PI * j / p->N);
+    tw[2 * j + 1] = -sin(2.0 * M_PI * j / p->N);
+  }
+  std::vector<float> twf(tw.begin(), tw.end());
   e = cudaMemset(p->dev_err, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->fft_tw, p->fp64 ? (const void *)tw.data() : (const void *)twf.data(),
+                   rs * 2 * (size_t)p->N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = build_tables(*p, 0);
@@ -433,19 +456,38 @@ matcha_status matcha_align(matcha_plan plan, const float *particles, const float
   if (np > Plan::NSPLIT) np = Plan::NSPLIT;
   CK(cudaEventRecord(p->ev_fork, st));
   const size_t vox = (size_t)p->N * p->N * p->N;
+  // Parts k >= joined (k > 0) have been forked and have recorded their join
+  // event.  An error in one part still joins every forked part back into the
+  // caller's stream, so no fork is left open (in a capture, or for the
+  // ordering of later work on `stream`).
+  int joined = np;
+  s = MATCHA_OK;
   for (int k = np - 1; k >= 0; --k) {
     const int b0 = (int)((long)B * k / np), b1 = (int)((long)B * (k + 1) / np);
     cudaStream_t sk = k ? p->split_stream[k - 1] : st;
-    if (k) CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
+    if (k) {
+      cudaError_t e = cudaStreamWaitEvent(sk, p->ev_fork, 0);
+      if (e != cudaSuccess) { s = fail_cuda(e, "matcha_align fork"); break; }
+    }
     const AlignWs wk = ws_at(*p, w, b0, tstride);
-    if ((s = align_range(plan, particles + vox * b0, tstride ? templates + vox * b0 : templates,
-                         b1 - b0, tstride, h_ready, P_per ? P_per + b0 : nullptr, euler + 3 * b0,
-                         R + 9 * b0, score + b0, best_p + b0, flags + b0, wk, sk)))
-      return s;
-    if (k) CK(cudaEventRecord(p->ev_join[k - 1], sk));
+    s = align_range(plan, particles + vox * b0, tstride ? templates + vox * b0 : templates,
+                    b1 - b0, tstride, h_ready, P_per ? P_per + b0 : nullptr, euler + 3 * b0,
+                    R + 9 * b0, score + b0, best_p + b0, flags + b0, wk, sk);
+    if (k) {
+      cudaError_t e = cudaEventRecord(p->ev_join[k - 1], sk);
+      if (e != cudaSuccess) {
+        if (s == MATCHA_OK) s = fail_cuda(e, "matcha_align join");
+        break;
+      }
+      joined = k;
+    }
+    if (s != MATCHA_OK) break;
   }
-  for (int k = 1; k < np; ++k) CK(cudaStreamWaitEvent(st, p->ev_join[k - 1], 0));
-  return MATCHA_OK;
+  for (int k = joined; k < np; ++k) {
+    cudaError_t e = cudaStreamWaitEvent(st, p->ev_join[k - 1], 0);
+    if (e != cudaSuccess && s == MATCHA_OK) s = fail_cuda(e, "matcha_align join");
+  }
+  return s;
 }
 
 // Host-buffer path: the batch is split into up to 8 chunks (of at least 128

@@ -11,22 +11,29 @@
 //
 // Work layout: one CTA per particle holds all P candidates.  A warp is split
 // into sub-slots of `cpw` lanes (cpw = P rounded up to a power of two); lane
-// p of a sub-slot follows candidate p, and a sub-slot walks one order pair at
-// a time, so the coefficient loads c^l and the recurrence coefficients of a
-// step are warp broadcasts.  Per-lane partial sums are reduced in a fixed
-// order (shuffles, then warps in index order, in FP64), so results do not
-// depend on scheduling.
+// p of a sub-slot follows candidate p.  A sub-slot walks partner groups (the
+// two order pairs (m, n), (m, n+1) of one m, stored interleaved), and each
+// lane advances both pairs of a group with paired (FP32x2 / 2 x FP64)
+// operations, so every lane reads its own copy of c^l and of the recurrence
+// coefficients from shared memory (staged per group with cp.async); nothing
+// is broadcast.  Per-lane partial sums are reduced in a fixed order (the two
+// halves, shuffles across sub-slots, then warps in index order), all in the
+// plan's working precision and converted to FP64 at the end, so results do
+// not depend on scheduling.
 //
 // Step rule (the paper gives only the plain update theta - H^{-1} grad):
 //   delta = -H^{-1} grad when -H is positive definite (Cholesky pivots
-//   > 1e-12 ||H||_F), else grad / ||H||_F (flag bit 1); ||delta|| clamped to
-//   pi / (2 (L+1)); the level ends early when ||delta|| < step_tol
-//   (Section 2.4); trial theta' = wrap(theta + delta) is accepted when
+//   > 1e-12 ||H||_F for FP64 sums, > 1e-6 ||H||_F for FP32 sums), else
+//   grad / ||H||_F (flag bit 1); ||delta|| clamped to pi / (2 (L+1)); the
+//   level ends early when ||delta|| < step_tol (Section 2.4); trial
+//   theta' = wrap(theta + delta) is accepted when
 //   C(theta') >= C(theta) - acc_tol |C(theta)| (acc_tol above the rounding
 //   level of the sums), else delta is halved (at most twice); three
 //   rejected trials end the level for that candidate (flag bit 2), since a
-//   repeated step from the same point would reject again.  Angles, the 3x3
-//   solve and the acceptance test are FP64 in both precisions.
+//   repeated step from the same point would reject again.  Angles, the
+//   acceptance test and the scores are FP64 in every plan; the 3x3 solve is
+//   FP64 on the final level and in the plan's precision (FP32 for the 32-bit
+//   plans) on the earlier levels.
 #include <math.h>
 #include "internal.cuh"
 
@@ -39,6 +46,7 @@ enum { ST_RUN = 0, ST_TRIAL = 1, ST_STOP = 2, ST_DEAD = 3 };
 
 struct NewtonArgs {
   int LJ, nlev, M, P, cpw, nslots;
+  int grad;  // 1: gradient steps grad / ||H||_F instead of Newton steps
   int Ls[MATCHA_MAX_LEVELS];
   double tol, acc_tol;
   long nc;
@@ -496,8 +504,8 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
     }
     cp_async_wait<0>();
   }
-  // both halves, then the sub-slots of the warp that follow the same candidate
-  // (working precision; the cross-warp sum below is FP64)
+  // both halves, then the sub-slots of the warp that follow the same candidate,
+  // then (below) the warps in index order: all in the working precision
   const int nq = FULL ? 10 : 1;
   T r[10];
 #pragma unroll
@@ -546,7 +554,8 @@ __device__ __forceinline__ void wrap_d(double *v) {
 // above piv_rel ||H||_F, set by the precision H was summed in (1e-12 for FP64
 // sums, 1e-6 for FP32 sums: above the rounding level of H's entries).
 template <typename S>
-__device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d, double piv_rel) {
+__device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d, double piv_rel,
+                                          bool grad) {
   S hn = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) hn += H[i] * H[i];
@@ -554,7 +563,7 @@ __device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d, d
   const S tol = S(piv_rel) * hn;
   // Cholesky of A = -H
   S a00 = -H[0], a10 = -H[3], a20 = -H[6], a11 = -H[4], a21 = -H[7], a22 = -H[8];
-  bool ok = a00 > tol;
+  bool ok = !grad && a00 > tol;  // grad: the gradient method, never the Newton step
   S L00 = 0, L10 = 0, L20 = 0, L11 = 0, L21 = 0, L22 = 0;
   if (ok) {
     L00 = sqrt(a00); L10 = a10 / L00; L20 = a20 / L00;
@@ -577,7 +586,7 @@ __device__ __forceinline__ int newton_dir(const S *g, const S *H, int L, S *d, d
     S x0 = (y0 - L10 * x1 - L20 * x2) / L00;
     d[0] = x0; d[1] = x1; d[2] = x2;
   } else {
-    fl = 2;
+    fl = grad ? 0 : 2;
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = hn > 0 ? g[i] / hn : S(0);
   }
@@ -612,7 +621,7 @@ __device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, 
     return;
   }
   S d[3];
-  sm.fl[tid] |= newton_dir<S>(g, H, L, d, piv_rel);
+  sm.fl[tid] |= newton_dir<S>(g, H, L, d, piv_rel, A.grad != 0);
   if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < S(A.tol)) {
     sm.state[tid] = ST_STOP;
     return;
@@ -796,6 +805,7 @@ cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, d
   for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
   A.tol = p.step_tol;
   A.acc_tol = p.accept_tol;
+  A.grad = p.refine;
   A.nc = p.nc;
   size_t smem = newton_smem_bytes(p, sizeof(T), A.nslots);
   cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

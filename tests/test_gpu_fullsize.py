@@ -1,8 +1,11 @@
 """The 1024-particle 64^3 batch (final L = 32) at full size, in the launch
-configuration the bench times: FP64 results checked against the oracle on a
-sample of particles, FP32 results checked on every particle against the
-oracle-checked FP64 GPU results (0.05 degrees) and on the sample against the
-oracle itself."""
+configuration the bench times, against the FP64 oracle on EVERY particle (the
+metric's accuracy gate): the FP64 path within 1e-8 rad and 1e-10 in score,
+the FP32, TF32 and BF16 paths within 0.05 degrees.  Particles whose two best
+oracle candidates sit in different basins with scores within 1e-6 relative
+(near-ties, where the argmax may legitimately differ) are checked apart: the
+chosen candidate's oracle-refined score must be within that margin of the
+best.  The oracle run takes a few minutes on the host cores."""
 import math
 
 import numpy as np
@@ -16,7 +19,6 @@ from gpu_helpers import oracle_align
 
 pytestmark = pytest.mark.gpu
 W = synth.WORKLOADS["batch64"]
-SAMPLE = [0, 1, 511, 1023]
 
 
 @pytest.fixture(scope="module")
@@ -29,33 +31,58 @@ def batch():
 
 @pytest.fixture(scope="module")
 def reference(batch):
-    parts = batch["particles"][SAMPLE].cpu().numpy()
-    temps = batch["templates"][SAMPLE].cpu().numpy()
+    parts = batch["particles"].cpu().numpy()
+    temps = batch["templates"].cpu().numpy()
     return oracle_align(W, parts, temps)
 
 
-@pytest.fixture(scope="module")
-def fp64_result(batch):
-    plan = m.plan_for_workload(W, precision=m.FP64)
+def near_ties(ref, rel=1e-6, distinct_deg=1.0):
+    ties = np.zeros(W.B, dtype=bool)
+    for b in range(W.B):
+        sc, eu, k = ref["cand_score"][b], ref["cand_euler"][b], int(ref["n_cand"][b])
+        order = np.argsort(-sc[:k], kind="stable")
+        Rb = O.euler_to_matrix(*eu[order[0]])
+        for q in order[1:]:
+            if math.degrees(O.rotation_angle(O.euler_to_matrix(*eu[q]), Rb)) > distinct_deg:
+                ties[b] = sc[order[0]] - sc[q] < rel * abs(sc[order[0]])
+                break
+    return ties
+
+
+def run(plan, batch):
     out = m.matcha_align(plan, batch["particles"], batch["templates"])
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def test_fp64_full_batch_matches_oracle_on_sample(fp64_result, reference):
-    for i, b in enumerate(SAMPLE):
-        assert O.rotation_angle(fp64_result["R"][b], reference["R"][i]) < 1e-8
-        assert abs(fp64_result["score"][b] - reference["score"][i]) <= 1e-10 * abs(reference["score"][i])
-    assert np.all(np.isfinite(fp64_result["score"]))
+def test_fp64_full_batch_matches_oracle_on_every_particle(batch, reference):
+    got = run(m.plan_for_workload(W, precision=m.FP64), batch)
+    ties = near_ties(reference)
+    print("near-ties: %d of %d" % (ties.sum(), W.B))
+    assert np.all(np.isfinite(got["score"]))
+    worst_a, worst_s = 0.0, 0.0
+    for b in range(W.B):
+        if ties[b]:
+            # the chosen candidate is one of the tied maxima
+            bp = int(got["best_p"][b])
+            assert reference["cand_score"][b, bp] >= reference["score"][b] * (1 - 1e-6)
+            continue
+        a = O.rotation_angle(got["R"][b], reference["R"][b])
+        s = abs(got["score"][b] - reference["score"][b]) / abs(reference["score"][b])
+        worst_a, worst_s = max(worst_a, a), max(worst_s, s)
+        assert a < 1e-8, (b, a)
+        assert s <= 1e-10, (b, s)
+    print("fp64 vs oracle, all %d particles: max %.2e rad, max score rel %.2e" % (W.B, worst_a, worst_s))
 
 
-def test_fp32_full_batch_within_005_degrees(batch, fp64_result, reference):
-    plan = m.plan_for_workload(W, precision=m.FP32)
-    out = m.matcha_align(plan, batch["particles"], batch["templates"])
-    R = out["R"].cpu().numpy()
-    errs = np.array([O.rotation_angle(R[b], fp64_result["R"][b]) for b in range(W.B)])
-    print("fp32 vs fp64 GPU: max %.3e deg, p90 %.3e deg" % (math.degrees(errs.max()),
-                                                           math.degrees(np.percentile(errs, 90))))
-    assert math.degrees(errs.max()) < 0.05
-    for i, b in enumerate(SAMPLE):
-        assert math.degrees(O.rotation_angle(R[b], reference["R"][i])) < 0.05
+@pytest.mark.parametrize("precision", [m.FP32, m.TF32, m.BF16], ids=["fp32", "tf32", "bf16"])
+def test_32bit_full_batch_within_005_degrees_of_oracle(batch, reference, precision):
+    got = run(m.plan_for_workload(W, precision=precision), batch)
+    ties = near_ties(reference)
+    errs = np.array([math.degrees(O.rotation_angle(got["R"][b], reference["R"][b])) for b in range(W.B)])
+    keep = ~ties
+    print("%s vs oracle: max %.3e deg, p90 %.3e deg over %d particles (%d near-ties apart, max %s)"
+          % ({m.FP32: "fp32", m.TF32: "tf32", m.BF16: "bf16"}[precision], errs[keep].max(),
+             np.percentile(errs[keep], 90), keep.sum(), ties.sum(),
+             "%.3e" % errs[ties].max() if ties.any() else "-"))
+    assert errs[keep].max() < 0.05

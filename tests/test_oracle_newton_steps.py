@@ -164,3 +164,46 @@ def test_step_tol_ends_the_level_after_converging_steps():
     xs, ss, fs = O.newton_march(c, [L], 3, np.array(g_true))
     assert np.array_equal(xs, np.array(g_true)) and fs == 0
     assert abs(ss - brute_C(f, h, S, R, L, g_true)) < 1e-10 * abs(ss)
+
+
+def test_gradient_direction_is_the_scaled_gradient():
+    g = np.array([0.01, -0.02, 0.005])
+    H = -np.array([[4.0, 1.0, 0.5], [1.0, 3.0, 0.2], [0.5, 0.2, 2.0]])
+    d = O.gradient_direction(g, H, 32)
+    assert np.abs(d - g / np.linalg.norm(H)).max() < 1e-18
+    d = O.gradient_direction(np.array([10.0, 0, 0]), H, 8)        # clamped
+    assert abs(np.linalg.norm(d) - math.pi / 18) < 1e-15 and d[0] > 0
+
+
+def test_gradient_steps_converge_linearly_and_newton_faster():
+    """Section 5.1's comparison: near a planted maximum the gradient method
+    climbs monotonically but needs many more steps than Newton for the same
+    accuracy."""
+    L, S, R = 8, 3, 5.0
+    rng = np.random.default_rng(3)
+    f = rand_coef(L, S, rng)
+    g_true = (1.0, 1.2, 2.0)
+    h = np.zeros_like(f)
+    for s in range(S):
+        for l in range(L + 1):
+            full = np.array([f[s, O.lm_index(l, n)] if n >= 0 else (-1) ** n * np.conj(f[s, O.lm_index(l, -n)])
+                             for n in range(-l, l + 1)])
+            hr = O.wigner_D(l, *g_true).conj().T @ full
+            for m in range(l + 1):
+                h[s, O.lm_index(l, m)] = hr[m + l]
+    c = O.correlate(f, h, S, R, L)
+    Rt = O.euler_to_matrix(*g_true)
+    t0 = np.array(g_true) + np.array([0.05, -0.04, 0.03])
+    err = lambda x: O.rotation_angle(O.euler_to_matrix(*x), Rt)
+    xn, sn, _ = O.newton_march(c, [L], 3, t0.copy(), step_tol=0)
+    prev, scores = err(t0), []
+    for k in (1, 2, 3, 6, 12):
+        xg, sg, fl = O.newton_march(c, [L], k, t0.copy(), step_tol=0, method=1)
+        scores.append(sg)
+        assert err(xg) < prev and fl & 2 == 0
+        prev = err(xg)
+    assert all(b >= a for a, b in zip(scores, scores[1:]))
+    xg3, _, _ = O.newton_march(c, [L], 3, t0.copy(), step_tol=0, method=1)
+    assert err(xn) < 1e-9 and err(xg3) > 100 * err(xn)
+    xg, _, _ = O.newton_march(c, [L], 200, t0.copy(), step_tol=1e-12, method=1)
+    assert err(xg) < 1e-6
