@@ -389,3 +389,18 @@ def template_grad_batch(f, h, euler, *, S, r_max, L_sched, wt=None, N=0, n_threa
                                   ctypes.c_int(B), _d(e), _d(w) if w is not None else None,
                                   _d(G), _d(out4), _i(flags), ctypes.c_int(n_threads))
     return (G[0::2] + 1j * G[1::2]).reshape(B, S, lm_size(L)), out4, flags
+
+
+def align_from_c(c, *, L0, K, P, M_iter, L_sched, step_tol=1e-9, accept_tol=1e-11, refine=0):
+    """Algorithm 1 from one pair's correlation coefficients (oracle layout, up to L_J)."""
+    p = make_params(0, 0, 0.0, L0, K, P, M_iter, L_sched, step_tol, accept_tol, refine)
+    ca = _split(np.asarray(c))
+    out = dict(euler=np.zeros(3), R=np.zeros(9), score=np.zeros(1), best_p=np.zeros(1, dtype=np.int32),
+               flags=np.zeros(1, dtype=np.int32), cand_idx=np.full(P, -1, dtype=np.int32),
+               cand_euler=np.zeros((P, 3)), cand_score=np.full(P, np.nan),
+               n_cand=np.zeros(1, dtype=np.int32))
+    lib().orc_align_from_c(ctypes.byref(p), _d(ca), ctypes.c_int(P), _d(out["euler"]), _d(out["R"]),
+                           _d(out["score"]), _i(out["best_p"]), _i(out["flags"]), _i(out["cand_idx"]),
+                           None, _d(out["cand_euler"]), _d(out["cand_score"]), _i(out["n_cand"]))
+    out["R"] = out["R"].reshape(3, 3)
+    return out

@@ -26,21 +26,17 @@ int orc_max_threads(void) {
 #endif
 }
 
-/* Algorithm 1 from the SH coefficients of the particle (f) and the template
- * (h), complex [S][lm] at L_J: everything after the analysis. */
-int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, int P_this,
-                        double *euler, double *R, double *score, int *best_p, int *flags,
-                        int *cand_idx, double *cand_euler0, double *cand_euler,
-                        double *cand_score, int *n_cand) {
-  int LJ = p->L_sched[p->n_levels - 1];
-  double *c = (double *)malloc(sizeof(double) * 2 * (size_t)orc_c_size(LJ));
+/* Algorithm 1 from the correlation coefficients c^l_mn (complex, the
+ * oracle's layout, up to L_J): the SOFFT search, the march, the argmax. */
+int orc_align_from_c(const orc_params *p, const double *c, int P_this, double *euler, double *R,
+                     double *score, int *best_p, int *flags, int *cand_idx, double *cand_euler0,
+                     double *cand_euler, double *cand_score, int *n_cand) {
   int n = orc_soft_n(p->L0, p->K);
   double *grid = (double *)malloc(sizeof(double) * (size_t)n * n * n);
   int P = P_this;
   int idx[P > 0 ? P : 1];
   double sc[P > 0 ? P : 1];
 
-  orc_correlate(f, h, p->S, p->r_max, LJ, c);
   orc_soft_grid(c, p->L0, p->K, grid);
   int nc = orc_local_maxima_topk(grid, n, P, idx, sc);
 
@@ -77,8 +73,23 @@ int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, i
   *best_p = best;
   *flags = fl;
   if (n_cand) *n_cand = nc;
-  free(c); free(grid);
+  free(grid);
   return 0;
+}
+
+/* Algorithm 1 from the SH coefficients of the particle (f) and the template
+ * (h), complex [S][lm] at L_J: everything after the analysis. */
+int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, int P_this,
+                        double *euler, double *R, double *score, int *best_p, int *flags,
+                        int *cand_idx, double *cand_euler0, double *cand_euler,
+                        double *cand_score, int *n_cand) {
+  int LJ = p->L_sched[p->n_levels - 1];
+  double *c = (double *)malloc(sizeof(double) * 2 * (size_t)orc_c_size(LJ));
+  orc_correlate(f, h, p->S, p->r_max, LJ, c);
+  int rc = orc_align_from_c(p, c, P_this, euler, R, score, best_p, flags, cand_idx, cand_euler0,
+                            cand_euler, cand_score, n_cand);
+  free(c);
+  return rc;
 }
 
 int orc_align_one(const orc_params *p, const float *particle, const float *tmpl, int P_this,

@@ -104,6 +104,9 @@ int orc_align_batch(const orc_params *p, const float *particles, const float *te
                     double *euler, double *R, double *score, int *best_p, int *flags,
                     int *cand_idx, double *cand_euler0, double *cand_euler,
                     double *cand_score, int *n_cand, int n_threads);
+int orc_align_from_c(const orc_params *p, const double *c, int P_this, double *euler, double *R,
+                     double *score, int *best_p, int *flags, int *cand_idx, double *cand_euler0,
+                     double *cand_euler, double *cand_score, int *n_cand);
 int orc_align_coefs_one(const orc_params *p, const double *f, const double *h, int P_this,
                         double *euler, double *R, double *score, int *best_p, int *flags,
                         int *cand_idx, double *cand_euler0, double *cand_euler,
