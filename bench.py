@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-pose6d", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-study", action="store_true")
     ap.add_argument("--no-oracle-gate", action="store_true",
                     help="skip the oracle run over the whole batch (accuracy against the oracle)")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
@@ -450,6 +452,123 @@ def time_pose6d(st, reps=3):
                            "shift_vox_p90": float(np.percentile(sh, 90))}}
 
 
+def time_precision(st, reps=2, sample=8):
+    """The precision workload (2048 pairs of 64^3, S = 32, final L = 48):
+    matcha_align timed in FP64, FP32, TF32 and BF16 plans (eager), and for a
+    sample of particles the error of every path against the FP64 oracle:
+    the refined rotation against the oracle's whole path, and C_L, its
+    gradient and Hessian (matcha_objective on the path's own coefficients)
+    against the oracle's objective at the path's refined rotation."""
+    import torch
+    import oracle
+    import paper_2603_15285_gb300 as m
+    import synth
+    w = synth.WORKLOADS["deep64"]
+    d = synth.make_batch(w, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    B = parts.shape[0]
+    L, S, R = w.L_sched[-1], w.n_shells, w.r_max
+    ps, ts = parts[:sample].cpu().numpy(), temps[:sample].cpu().numpy()
+    ref = oracle.align_batch(ps, ts, S=S, r_max=R, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter,
+                             L_sched=w.L_sched)
+    cor = [oracle.correlate(oracle.analyze_volume(ps[b], S, R, L), oracle.analyze_volume(ts[b], S, R, L),
+                            S, R, L) for b in range(sample)]
+    out = {"workload": "deep64: %d pairs of 64^3, S=%d, L %s, P=%d; errors on the first %d particles"
+                       % (B, S, "->".join(map(str, w.L_sched)), w.P, sample)}
+    for name, prec in (("fp64", m.FP64), ("fp32", m.FP32), ("tf32", m.TF32), ("bf16", m.BF16)):
+        plan = m.plan_for_workload(w, precision=prec)
+        ws = m.alloc_workspace(plan, B)
+        o = m.matcha_align(plan, parts, temps, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 1 if prec == m.FP64 else reps
+        e0.record(st)
+        for _ in range(k):
+            m.matcha_align(plan, parts, temps, ws=ws, out=o)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        del ws
+        eu = o["euler"][:sample].contiguous()
+        f = m.matcha_analyze(plan, parts[:sample].contiguous())
+        h = m.matcha_analyze(plan, temps[:sample].contiguous())
+        c = m.matcha_correlate_coeffs(plan, f, h, 1)
+        ob = m.matcha_objective(plan, c, eu[:, None, :].contiguous()).cpu().numpy()[:, 0]
+        Rg = o["R"][:sample].cpu().numpy()
+        ang, eC, eg, eH = [], [], [], []
+        for b in range(sample):
+            C, g, H, _ = oracle.objective(cor[b], L, *eu[b].cpu().numpy(), derivs=True)
+            eC.append(abs(ob[b, 0] - C) / abs(C))
+            eg.append(np.abs(ob[b, 1:4] - g).max() / abs(C))
+            Hv = np.array([H[0, 0], H[0, 1], H[0, 2], H[1, 1], H[1, 2], H[2, 2]])
+            eH.append(np.abs(ob[b, 4:] - Hv).max() / np.abs(Hv).max())
+            ang.append(math.degrees(oracle.rotation_angle(Rg[b], ref["R"][b])))
+        out[name] = {"ms_per_step": ms, "value": B / (ms * 1e-3), "unit": "particles/s",
+                     "angle_deg_max_vs_oracle": max(ang), "C_rel_max": max(eC),
+                     "grad_max_over_C": max(eg), "hessian_rel_max": max(eH)}
+        plan.close()
+    return out
+
+
+def time_refine_study(st, n=128):
+    """Section 5.1's comparisons on the 64^3 batch (first n particles, FP32):
+    refinement by Newton steps against gradient steps at several step counts
+    per level, and the dense SOFFT baseline (the best grid point, no
+    refinement) at increasing oversampling K; angular error against the
+    FP64 path's Newton result and against the planted rotation, and time."""
+    import dataclasses
+    import torch
+    import oracle
+    import paper_2603_15285_gb300 as m
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    d = synth.make_batch(w, B=n, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    p64 = m.plan_for_workload(w, precision=m.FP64)
+    Rref = m.matcha_align(p64, parts, temps)["R"].cpu().numpy()
+    p64.close()
+
+    def timed(fn, k=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k):
+            r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / k
+
+    def errs(R):
+        a = np.degrees([oracle.rotation_angle(R[b], Rref[b]) for b in range(n)])
+        t = np.degrees([oracle.rotation_angle(R[b], d["R_true"][b]) for b in range(n)])
+        return {"p90_deg_vs_fp64_newton": float(np.percentile(a, 90)), "max_deg_vs_fp64_newton": float(a.max()),
+                "p90_deg_vs_planted": float(np.percentile(t, 90))}
+    out = {"workload": "first %d particles of batch64, FP32" % n, "newton": {}, "gradient": {}, "dense_soft": {}}
+    for refine, key, steps in ((0, "newton", (1, 2, 3, 5)), (1, "gradient", (1, 3, 10, 30))):
+        for M in steps:
+            plan = m.plan_for_workload(dataclasses.replace(w, M_iter=M), precision=m.FP32, refine=refine)
+            ws = m.alloc_workspace(plan, n)
+            o, ms = timed(lambda: m.matcha_align(plan, parts, temps, ws=ws))
+            out[key]["M=%d" % M] = dict(errs(o["R"].cpu().numpy()), ms=ms)
+            del ws
+            plan.close()
+    for K in (2, 4, 8, 16):
+        wk = dataclasses.replace(w, K=K, P=1)
+        plan = m.plan_for_workload(wk, precision=m.FP32)
+        f = m.matcha_analyze(plan, parts)
+        h = m.matcha_analyze(plan, temps)
+        c = m.matcha_correlate_coeffs(plan, f, h, 1)
+        grid = torch.empty((n,) + (plan.info.soft_n,) * 3, dtype=torch.float32, device="cuda")
+        s, ms = timed(lambda: m.matcha_soft_search(plan, c, grid=grid))
+        eu = s["euler"][:, 0].cpu().numpy()
+        R = np.stack([oracle.euler_to_matrix(*eu[b]) for b in range(n)])
+        out["dense_soft"]["K=%d" % K] = dict(errs(R), ms=ms, points_per_angle=plan.info.soft_n)
+        del grid
+        plan.close()
+    return out
+
+
 def run_reference(args):
     """The oracle (FP64 C, all host cores) on a bounded sample of the workload."""
     ws, rank, _ = dist_env()
@@ -733,6 +852,14 @@ def main():
         res["backward"] = time_backward(st)
     if rank == 0 and not args.no_mixed:
         res["mixed"] = time_mixed(st, prec)
+        import torch
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_precision:
+        res["precision"] = time_precision(st)
+        import torch
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_study:
+        res["refine_study"] = time_refine_study(st)
         import torch
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_pose6d:

@@ -60,7 +60,7 @@ extern "C" {
 #endif
 
 #define MATCHA_MAX_LEVELS 16
-#define MATCHA_MAX_L 64
+#define MATCHA_MAX_L 100
 #define MATCHA_MAX_P 32
 
 typedef struct matcha_plan_s *matcha_plan;
@@ -81,7 +81,9 @@ typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1, MATCHA_TF32 = 2, MATCHA_BF16 = 
  *   n_shells     S, Gauss-Legendre radial shells on (0, r_max] (1 .. 128)
  *   r_max        outer shell radius in voxels; <= 0 selects N/2 - 1
  *   L0           SOFFT bandwidth (Section 2.3), 1 .. 32, equal to L_sched[0]
- *   K_oversample SOFFT oversampling K (1 .. 4)
+ *   K_oversample SOFFT oversampling K (1 .. 16; grids beyond the fused
+ *                kernels go through memory, MATCHA_ERR_UNSUPPORTED when even
+ *                that kernel's per-slice tables do not fit)
  *   P_max        candidates kept per particle, 1 .. MATCHA_MAX_P
  *   M_iter       Newton steps per level, 1 .. 32
  *   n_levels     number of bandwidth levels J+1 (L_sched[0] = L0 is the
@@ -97,6 +99,15 @@ typedef enum { MATCHA_FP64 = 0, MATCHA_FP32 = 1, MATCHA_TF32 = 2, MATCHA_BF16 = 
  *   refine       0: Newton steps (Section 2.2); 1: gradient steps
  *                delta = grad / ||H||_F with the same clamp and step control,
  *                the first-order method Section 5.1 compares against.
+ *   ball_lambda  0: radial shells (c^l_mn = sum_s w_s f_lm(r_s) conj(h_ln(r_s)));
+ *                > 0: the ball-harmonic radial basis with the eigenvalue cut
+ *                Lambda (Appendix "Ball harmonics expansion and eigenvalue-
+ *                based truncation"): radial functions N_lk j_l(lambda_lk r/R),
+ *                lambda_lk the zeros of j_l up to Lambda (R = r_max), the
+ *                coefficients projected from the shells by the radial rule,
+ *                c^l_mn = sum_{k in K_l} f_klm conj(h_kln) (Eq. sigmalmm,
+ *                rank <= |K_l|).  Needs 1 <= |K_0| <= n_shells; not with
+ *                MATCHA_TF32 / MATCHA_BF16 nor with the template gradient.
  * The angular sampling is n_theta = L_J + 1 Gauss-Legendre nodes in cos(theta)
  * and n_phi = 2 L_J + 2 equispaced phi per shell. */
 typedef struct {
@@ -113,6 +124,7 @@ typedef struct {
   double step_tol;
   double accept_tol;
   int refine;
+  double ball_lambda;
 } matcha_plan_desc;
 
 /* Sizes derived from a plan. */
@@ -220,6 +232,15 @@ matcha_status matcha_soft_search_noalloc(matcha_plan plan, const void *c_dev, in
 matcha_status matcha_newton_march(matcha_plan plan, const void *c_dev, int B,
                                   const int *n_cand_dev, double *euler_dev, double *score_dev,
                                   int *cand_flags_dev, long long *work_dev, void *stream);
+
+/* C_L and its analytic gradient and Hessian in the Euler angles (Section
+ * 2.2, Appendix A.4: d/da brings i m, d/dg brings i n, d/db acts on d^l) at
+ * Q <= P_max rotations per particle, summed exactly as the refinement sums
+ * them (plan precision, per-degree rescaling above L_J = 64 in the 32-bit
+ * plans).  euler_dev [B][Q][3]; out_dev [B][Q][10] doubles: C, C_a, C_b,
+ * C_g, C_aa, C_ab, C_ag, C_bb, C_bg, C_gg.  0 <= L <= L_J. */
+matcha_status matcha_objective(matcha_plan plan, const void *c_dev, int B, int L, int Q,
+                               const double *euler_dev, double *out_dev, void *stream);
 
 /* a7: argmax_p C_{L_J} (ties to the smaller p, NaN skipped), Euler -> matrix.
  * flags_dev [B]: OR of the candidates' flags, plus bit 3 when fewer than P_b

@@ -52,6 +52,9 @@ void orc_analyze_volume(const float *vol, int N, int S, double R, int L, double 
   int nt = L + 1, np = 2 * L + 2, nlm = orc_lm_size(L);
   double *smp = (double *)malloc(sizeof(double) * (size_t)S * nt * np);
   orc_sample_shells(vol, N, S, R, L, smp);
+  /* shells are independent; inside an already parallel batch this runs on
+     the calling thread (no nested parallelism) */
+#pragma omp parallel for schedule(dynamic)
   for (int s = 0; s < S; ++s)
     orc_sh_analyze_shell(smp + (long)s * nt * np, L, coef + 2L * s * nlm);
   free(smp);

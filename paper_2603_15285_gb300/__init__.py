@@ -31,7 +31,7 @@ SYMBOLS = [
     "matcha_soft_search_noalloc", "matcha_template_grad_workspace_size", "matcha_template_grad",
     "matcha_plan_device_status", "matcha_plan_autotune", "matcha_plan_set_wait_limit",
     "matcha_transform_volumes", "matcha_shift_search_workspace_size", "matcha_shift_search",
-    "matcha_align6d_workspace_size", "matcha_align6d",
+    "matcha_align6d_workspace_size", "matcha_align6d", "matcha_objective",
 ]
 
 
@@ -45,7 +45,7 @@ class PlanDesc(ctypes.Structure):
                 ("M_iter", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("L_sched", ctypes.c_int * MATCHA_MAX_LEVELS), ("precision", ctypes.c_int),
                 ("step_tol", ctypes.c_double), ("accept_tol", ctypes.c_double),
-                ("refine", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("ball_lambda", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib():
             "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_transform_volumes": [i, _vp, i, i, _vp, _vp, i, _vp, _vp],
+            "matcha_objective": [_vp, _vp, i, i, i, _vp, _vp, _vp],
             "matcha_shift_search_workspace_size": [_vp, i, i, i, ctypes.POINTER(sz)],
             "matcha_shift_search": [_vp, _vp, _vp, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_align6d_workspace_size": [_vp, i, i, i, i, ctypes.POINTER(sz)],
@@ -138,7 +139,8 @@ class Plan:
 
     def __init__(self, box_n: int, n_shells: int, L0: int, K: int, P: int, M_iter: int,
                  L_sched: Sequence[int], precision: int = FP64, r_max: float = 0.0,
-                 step_tol: float = 0.0, accept_tol: float = 0.0, refine: int = 0):
+                 step_tol: float = 0.0, accept_tol: float = 0.0, refine: int = 0,
+                 ball_lambda: float = 0.0):
         _torch()
         d = PlanDesc()
         d.box_n, d.n_shells, d.r_max = box_n, n_shells, r_max
@@ -150,6 +152,7 @@ class Plan:
             d.L_sched[k] = int(L)
         d.precision, d.step_tol, d.accept_tol = precision, step_tol, accept_tol
         d.refine = refine
+        d.ball_lambda = ball_lambda
         h = _vp()
         _check(lib().matcha_plan_create(ctypes.byref(d), ctypes.byref(h)), "matcha_plan_create")
         self._h = h
@@ -313,6 +316,19 @@ def matcha_newton_march(plan: Plan, c, n_cand, euler, work=None, score=None, fla
     _check(lib().matcha_newton_march(plan.handle, _ptr(c), B, _ptr(n_cand), _ptr(euler), _ptr(score),
                                      _ptr(flags), _ptr(work), _stream()), "matcha_newton_march")
     return dict(euler=euler, score=score, flags=flags, work=work)
+
+
+def matcha_objective(plan: Plan, c, euler, L=None):
+    """C_L, gradient and Hessian at rotations euler [B][Q][3] (float64); returns
+    [B][Q][10] (C, C_a, C_b, C_g, C_aa, C_ab, C_ag, C_bb, C_bg, C_gg)."""
+    torch = _torch()
+    _need(c, plan.real_dtype, "c"); _need(euler, torch.float64, "euler")
+    B, Q = euler.shape[0], euler.shape[1]
+    out = torch.empty((B, Q, 10), dtype=torch.float64, device="cuda")
+    L = plan.L_final if L is None else L
+    _check(lib().matcha_objective(plan.handle, _ptr(c), B, L, Q, _ptr(euler), _ptr(out), _stream()),
+           "matcha_objective")
+    return out
 
 
 def matcha_final_select(plan: Plan, n_cand, cand_euler, cand_score, cand_flags, P_per=None):

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "_lib", "libmatcha.so")
 PROBE = os.path.join(HERE, "_lib", "libpeakprobe.so")
 SOURCES = ["matcha_api.cu", "plan_tables.cu", "analyze.cu", "correlate.cu", "soft.cu", "newton.cu",
-           "noalloc.cu", "backward.cu", "translate.cu", "pose6d.cu",
+           "noalloc.cu", "backward.cu", "translate.cu", "pose6d.cu", "ball.cu",
            "correlate_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -37,57 +37,62 @@ __device__ __forceinline__ T trilinear(const float *__restrict__ vol, int N, T p
   return wz0 * a0 + wz1 * a1;
 }
 
+// The rings are sampled and transformed RB at a time (the samples of RB
+// rings, then their phi DFTs into F), so the shared memory holds F and RB
+// rings rather than every sample of the shell: this kernel serves the
+// bandwidths the shell-group kernel cannot hold (up to L_J = 100 in FP64).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_analyze(const float *__restrict__ vols, int N, int S, int L, const double *__restrict__ rs,
           const double *__restrict__ xj, const T *__restrict__ ptabT, const T *__restrict__ phi_cs,
-          T *__restrict__ out) {
+          T *__restrict__ out, int RB) {
   const int s = blockIdx.x;
   const long b = blockIdx.y;
   const int nt = L + 1, np = 2 * L + 2, nm = L + 1, nlm = (L + 1) * (L + 2) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *smp = reinterpret_cast<T *>(smem_raw);  // [nt][np]
-  T *F = smp + nt * np;                       // [nt][nm] complex
-  T *tw = F + 2 * nt * nm;                    // [np][2]
+  T *F = reinterpret_cast<T *>(smem_raw);  // [nt][nm] complex
+  T *tw = F + 2 * nt * nm;                  // [np][2]
+  T *smp = tw + 2 * np;                     // [RB][np]
   const float *vol = vols + b * N * N * N;
   const T r = (T)rs[s];
   const T c0 = (T)(0.5 * N);
   for (int k = threadIdx.x; k < 2 * np; k += blockDim.x) tw[k] = phi_cs[k];
   __syncthreads();
 
-  const int total = nt * np, NT = blockDim.x;
-  for (int base = threadIdx.x; base < total; base += 2 * NT) {
-    int id1 = base + NT;
-    int j0 = base / np, k0 = base - j0 * np;
-    int id1c = id1 < total ? id1 : base;
-    int j1 = id1c / np, k1 = id1c - j1 * np;
-    T x0 = (T)xj[j0], x1 = (T)xj[j1];
-    T st0 = sqrt(max(T(1) - x0 * x0, T(0))), st1 = sqrt(max(T(1) - x1 * x1, T(0)));
-    T v0 = trilinear<T>(vol, N, c0 + r * st0 * tw[2 * k0], c0 + r * st0 * tw[2 * k0 + 1], c0 + r * x0);
-    T v1 = trilinear<T>(vol, N, c0 + r * st1 * tw[2 * k1], c0 + r * st1 * tw[2 * k1 + 1], c0 + r * x1);
-    smp[base] = v0;
-    if (id1 < total) smp[id1] = v1;
-  }
-  __syncthreads();
-
-  const int half = np / 2;
-  for (int idx = threadIdx.x; idx < nt * nm; idx += blockDim.x) {
-    int j = idx / nm, m = idx - j * nm;
-    const T *row = smp + j * np;
-    T re = row[0] + ((m & 1) ? -row[half] : row[half]);
-    T im = 0;
-    int t = m;
-    for (int k = 1; k < half; ++k) {
-      T sp = row[k] + row[np - k], sm = row[k] - row[np - k];
-      re = fma(sp, tw[2 * t], re);
-      im = fma(-sm, tw[2 * t + 1], im);
-      t += m;
-      if (t >= np) t -= np;
+  const int NT = blockDim.x, half = np / 2;
+  for (int jr = 0; jr < nt; jr += RB) {
+    const int nr = min(RB, nt - jr), total = nr * np;
+    for (int base = threadIdx.x; base < total; base += 2 * NT) {
+      int id1 = base + NT;
+      int j0 = base / np, k0 = base - j0 * np;
+      int id1c = id1 < total ? id1 : base;
+      int j1 = id1c / np, k1 = id1c - j1 * np;
+      T x0 = (T)xj[jr + j0], x1 = (T)xj[jr + j1];
+      T st0 = sqrt(max(T(1) - x0 * x0, T(0))), st1 = sqrt(max(T(1) - x1 * x1, T(0)));
+      T v0 = trilinear<T>(vol, N, c0 + r * st0 * tw[2 * k0], c0 + r * st0 * tw[2 * k0 + 1], c0 + r * x0);
+      T v1 = trilinear<T>(vol, N, c0 + r * st1 * tw[2 * k1], c0 + r * st1 * tw[2 * k1 + 1], c0 + r * x1);
+      smp[base] = v0;
+      if (id1 < total) smp[id1] = v1;
     }
-    F[2 * idx] = re;
-    F[2 * idx + 1] = im;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
+      int jj = idx / nm, m = idx - jj * nm;
+      const T *row = smp + jj * np;
+      T re = row[0] + ((m & 1) ? -row[half] : row[half]);
+      T im = 0;
+      int t = m;
+      for (int k = 1; k < half; ++k) {
+        T sp = row[k] + row[np - k], sm = row[k] - row[np - k];
+        re = fma(sp, tw[2 * t], re);
+        im = fma(-sm, tw[2 * t + 1], im);
+        t += m;
+        if (t >= np) t -= np;
+      }
+      F[2 * ((jr + jj) * nm + m)] = re;
+      F[2 * ((jr + jj) * nm + m) + 1] = im;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   T *o = out + 2 * ((b * S + s) * (long)nlm);
   for (int lm = threadIdx.x; lm < nlm; lm += blockDim.x) {
@@ -356,14 +361,15 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
       return cudaGetLastError();
     }
   }
-  size_t smem = sizeof(T) * ((size_t)p.nt * p.np + 2 * (size_t)p.nt * (p.LJ + 1) + 2 * (size_t)p.np);
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    cudaFuncSetAttribute(k_analyze<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[sizeof(T) == 8] = true;
-  }
+  // rings per batch: as many as fit next to F (all of them when they do)
+  const size_t fixed = 2 * (size_t)p.nt * (p.LJ + 1) + 2 * (size_t)p.np;
+  int RB = p.nt;
+  while (RB > 1 && sizeof(T) * (fixed + (size_t)RB * p.np) > 220 * 1024) RB = (RB + 1) / 2;
+  size_t smem = sizeof(T) * (fixed + (size_t)RB * p.np);
+  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_analyze<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_analyze<T><<<dim3(p.S, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj, (const T *)p.ptab,
-                                                 (const T *)p.phi_cs, coef);
+                                                 (const T *)p.phi_cs, coef, RB);
   return cudaGetLastError();
 }
 

@@ -32,11 +32,20 @@ template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
 
-template <typename T>
+//
+// With BALL (plans with the ball-harmonic radial basis) the staged rows are
+// the projections on the retained radial functions instead of the shells:
+// f_klm = sum_s W_lk(s) f_lm(r_s), W_lk(s) = w_s N_lk j_l(lambda_lk r_s / R),
+// for k < |K_l| (both sides), and the products run over those |K_l| rows:
+// c^l_mn = sum_{k in K_l} f_klm conj(h_kln), Eq. (sigmalmm) itself, i.e. A_l
+// through its rank-|K_l| factors, so a degree costs |K_l| (2l+1)^2 products
+// instead of S (2l+1)^2.
+template <typename T, bool BALL>
 __global__ void __launch_bounds__(256)
 k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, long h_stride,
                 const double *__restrict__ wrad, const int *__restrict__ pair_base, long nc,
-                T *__restrict__ c) {
+                T *__restrict__ c, const T *__restrict__ ballW, const int *__restrict__ ballK,
+                int Kmax) {
   using C2 = typename Cplx<T>::type;
   const long b = blockIdx.y;
   const int nlm = (L + 1) * (L + 2) / 2;
@@ -49,18 +58,37 @@ k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, 
   const int npass = l_hi == l_lo ? 1 : 2;
   // stage: degree d's orders 0..l at [S][l+1] (F) and [S][l+1] (w H)
   const int no0 = l_lo + 1, no1 = l_hi + 1;
-  C2 *F0 = sF, *H0 = sF + S * no0, *F1 = sF + 2 * S * no0, *H1 = F1 + S * no1;
+  const int R0 = BALL ? Kmax : S;  // rows reserved per degree
+  C2 *F0 = sF, *H0 = sF + R0 * no0, *F1 = sF + 2 * R0 * no0, *H1 = F1 + R0 * no1;
+  // rows summed per degree: the shells, or the retained radial functions
+  const int S0 = BALL ? ballK[l_lo] : S, S1 = BALL ? ballK[l_hi] : S;
   for (int d = 0; d < npass; ++d) {
     const int l = d ? l_hi : l_lo, no = l + 1, base = l * (l + 1) / 2;
     C2 *Fd = d ? F1 : F0, *Hd = d ? H1 : H0;
-    for (int t = threadIdx.x; t < S * no; t += blockDim.x) {
-      int s = t / no, m = t - s * no;
-      long src = 2 * ((long)s * nlm + base + m);
-      T w = (T)wrad[s];
-      C2 fv, hv;
-      fv.x = fb[src]; fv.y = fb[src + 1];
-      hv.x = w * hb[src]; hv.y = w * hb[src + 1];
-      Fd[t] = fv; Hd[t] = hv;
+    if (BALL) {
+      const int Kl = d ? S1 : S0;
+      const T *Wl = ballW + (long)l * Kmax * S;
+      for (int t = threadIdx.x; t < Kl * no; t += blockDim.x) {
+        const int k = t / no, m = t - k * no;
+        C2 fv{T(0), T(0)}, hv{T(0), T(0)};
+        for (int s = 0; s < S; ++s) {
+          const T w = Wl[k * S + s];
+          const long src = 2 * ((long)s * nlm + base + m);
+          fv.x = fma(w, fb[src], fv.x); fv.y = fma(w, fb[src + 1], fv.y);
+          hv.x = fma(w, hb[src], hv.x); hv.y = fma(w, hb[src + 1], hv.y);
+        }
+        Fd[t] = fv; Hd[t] = hv;
+      }
+    } else {
+      for (int t = threadIdx.x; t < S * no; t += blockDim.x) {
+        int s = t / no, m = t - s * no;
+        long src = 2 * ((long)s * nlm + base + m);
+        T w = (T)wrad[s];
+        C2 fv, hv;
+        fv.x = fb[src]; fv.y = fb[src + 1];
+        hv.x = w * hb[src]; hv.y = w * hb[src + 1];
+        Fd[t] = fv; Hd[t] = hv;
+      }
     }
   }
   __syncthreads();
@@ -88,7 +116,8 @@ k_correlate_deg(const T *__restrict__ f, const T *__restrict__ h, int S, int L, 
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[u][v][k] = 0;
     const C2 *F = d ? F1 : F0, *H = d ? H1 : H0;
-    for (int s = 0; s < S; ++s, F += no, H += no) {
+    const int Sd = d ? S1 : S0;
+    for (int s = 0; s < Sd; ++s, F += no, H += no) {
       const C2 fa[2] = {F[a0], F[a1]}, hb[2] = {H[b0], H[b1]};
 #pragma unroll
       for (int u = 0; u < 2; ++u)
@@ -139,14 +168,23 @@ cudaError_t launch_correlate(const Plan &p, const T *f, const T *h, int B, int h
   if (B == 0) return cudaSuccess;
   if (sizeof(T) == 4 && p.tc)
     return launch_correlate_tc(p, (const float *)f, (const float *)h, B, hstride, (float *)c, st);
-  size_t smem = sizeof(T) * 4 * (size_t)p.S * (p.LJ + 2);  // both degrees of a pair
-  static bool attr[2] = {false, false};
-  if (!attr[sizeof(T) == 8]) {
-    cudaFuncSetAttribute(k_correlate_deg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr[sizeof(T) == 8] = true;
+  const bool ball = p.ball_kmax > 0;
+  const int rows = ball ? p.ball_kmax : p.S;
+  size_t smem = sizeof(T) * 4 * (size_t)rows * (p.LJ + 2);  // both degrees of a pair
+  static bool attr[2][2] = {{false, false}, {false, false}};
+  if (!attr[ball][sizeof(T) == 8]) {
+    cudaFuncSetAttribute(ball ? k_correlate_deg<T, true> : k_correlate_deg<T, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr[ball][sizeof(T) == 8] = true;
   }
-  k_correlate_deg<T><<<dim3(p.LJ / 2 + 1, B), 256, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad,
-                                                              p.pair_base, p.nc, c);
+  dim3 grid(p.LJ / 2 + 1, B);
+  if (ball)
+    k_correlate_deg<T, true><<<grid, 256, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad, p.pair_base,
+                                                      p.nc, c, (const T *)p.ball_W, p.ball_K,
+                                                      p.ball_kmax);
+  else
+    k_correlate_deg<T, false><<<grid, 256, smem, st>>>(f, h, p.S, p.LJ, hstride, p.wrad,
+                                                       p.pair_base, p.nc, c, nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 

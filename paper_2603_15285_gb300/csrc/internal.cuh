@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <vector>
 #include "../../include/matcha.h"
 
 namespace matcha {
@@ -42,6 +43,11 @@ struct Plan {
   int Qf, Mq;                   // folded DFT rows ceil(L_J/2); columns per order parity, padded to 4
   void *ring;                   // real [S * nt][2]: (r_s sin t_j, N/2 + r_s cos t_j) of ring s * nt + j
   void *fft_tw;                 // real [N][2]: cos, sin (-2 pi j / N), the box FFT's twiddles
+  // ball-harmonic radial basis (ball_kmax = 0: radial shells)
+  double ball_lambda = 0;       // frequency budget Lambda
+  int ball_kmax = 0;            // |K_0|, rows of the projection table
+  void *ball_W = nullptr;       // real [L_J+1][ball_kmax][S]: w_s N_lk j_l(lambda_lk r_s / R)
+  int *ball_K = nullptr;        // [L_J+1] |K_l| (in the same allocation as ball_W)
   int fft_npass = 0;            // radix passes of the length-N FFT (0: N has a factor > 5)
   int fft_radix[16] = {};       // radices (4, 2, 3, 5) in pass order
   int *pair_base;               // [npairs] first real of pair q in the grouped L_J layout
@@ -90,6 +96,11 @@ inline long pair_entries_host(int L) {  // sum_{m<=L} (2m+1)(L-m+1)
 
 // Table builders (plan_tables.cu).
 cudaError_t build_tables(Plan &p, cudaStream_t st);
+// The ball-harmonic radial table on the host (ball.cu): W[l][k][s] =
+// w_s N_lk j_l(lambda_lk r_s / R) for k < |K_l| (zero-padded to Kmax), the
+// counts |K_l|; returns Kmax = |K_0|.
+int ball_tables(int L, int S, double R, double Lam, const double *r, const double *w,
+                std::vector<double> &W, std::vector<int> &counts);
 
 // Kernel launchers; each returns cudaGetLastError() after its launches.
 template <typename T>
@@ -104,6 +115,9 @@ template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st);
 template <typename T>
+cudaError_t launch_objective(const Plan &p, const T *c, int B, int L, int Q, const double *pts,
+                             double *out, cudaStream_t st);
+template <typename T>
 cudaError_t launch_template_grad(const Plan &p, const T *f, const T *c, int B, int tstride,
                                  const double *euler, const double *weight, T *X, T *coef_grad,
                                  double *vox_grad, double *shift, int *flags, cudaStream_t st);
@@ -114,6 +128,7 @@ bool backward_fits(const Plan &p);  // the template-gradient kernel's shared mem
 bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 bool analyze_shells_ok(const Plan &p, int G);  // G shells per analysis CTA fit
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
+bool soft_fits(const Plan &p);           // some SOFFT kernel serves the plan
 // Translation search (translate.cu): volume poses, the box FFT, the cross
 // spectrum and the windowed inverse DFT of the correlation.
 cudaError_t launch_pose_volumes(int N, const float *vol, int B, long vol_stride, const double *R,

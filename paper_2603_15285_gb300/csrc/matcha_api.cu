@@ -99,7 +99,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   if (!d || !out) return MATCHA_ERR_INVALID_ARG;
   *out = nullptr;
   if (d->box_n < 4 || d->box_n > 512 || d->n_shells < 1 || d->n_shells > 128) return MATCHA_ERR_INVALID_ARG;
-  if (d->L0 < 1 || d->L0 > 32 || d->K_oversample < 1 || d->K_oversample > 4) return MATCHA_ERR_INVALID_ARG;
+  if (d->L0 < 1 || d->L0 > 32 || d->K_oversample < 1 || d->K_oversample > 16) return MATCHA_ERR_INVALID_ARG;
   if (d->P_max < 1 || d->P_max > MATCHA_MAX_P || d->M_iter < 1 || d->M_iter > 32) return MATCHA_ERR_INVALID_ARG;
   if (d->n_levels < 1 || d->n_levels > MATCHA_MAX_LEVELS) return MATCHA_ERR_INVALID_ARG;
   if (d->L_sched[0] != d->L0) return MATCHA_ERR_INVALID_ARG;
@@ -110,6 +110,12 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   if (!isfinite(d->r_max) || !isfinite(d->step_tol) || !isfinite(d->accept_tol))
     return MATCHA_ERR_INVALID_ARG;
   if (d->refine != 0 && d->refine != 1) return MATCHA_ERR_INVALID_ARG;
+  if (!isfinite(d->ball_lambda) || d->ball_lambda < 0) return MATCHA_ERR_INVALID_ARG;
+  if (d->ball_lambda > 0 && d->precision >= MATCHA_TF32) {
+    set_error_text("plan: the ball-harmonic radial basis runs on the CUDA-core contraction "
+                   "(FP64 and FP32 plans)");
+    return MATCHA_ERR_UNSUPPORTED;
+  }
 
   Plan *p = new Plan();
   p->desc = *d;
@@ -140,6 +146,15 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
     snprintf(msg, sizeof(msg),
              "plan: the refinement kernel's shared-memory tables do not fit for P_max = %d, "
              "L_J = %d in this precision", p->P, p->LJ);
+    delete p;
+    set_error_text(msg);
+    return MATCHA_ERR_UNSUPPORTED;
+  }
+  if (!soft_fits(*p)) {
+    char msg[160];
+    snprintf(msg, sizeof(msg),
+             "plan: no SOFFT kernel's shared memory fits L0 = %d with K = %d in this precision "
+             "(%d points per angle)", p->L0, p->K, p->ns);
     delete p;
     set_error_text(msg);
     return MATCHA_ERR_UNSUPPORTED;
@@ -211,6 +226,42 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
     delete p;
     return fail_cuda(e, "plan tables");
   }
+  if (d->ball_lambda > 0) {  // ball-harmonic radial table (host), then uploaded
+    p->ball_lambda = d->ball_lambda;
+    std::vector<double> r(p->S), w(p->S), W;
+    std::vector<int> counts;
+    e = cudaMemcpy(r.data(), p->rs, 8 * p->S, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(w.data(), p->wrad, 8 * p->S, cudaMemcpyDeviceToHost);
+    int kmax = e == cudaSuccess ? ball_tables(p->LJ, p->S, p->R, p->ball_lambda, r.data(), w.data(),
+                                              W, counts) : 0;
+    if (e == cudaSuccess && (kmax < 1 || kmax > p->S)) {
+      char msg[200];
+      snprintf(msg, sizeof(msg),
+               "plan: Lambda = %g keeps %d radial functions at l = 0; the ball basis needs "
+               "1 .. n_shells (%d)", p->ball_lambda, kmax, p->S);
+      cudaFree(p->base);
+      delete p;
+      set_error_text(msg);
+      return MATCHA_ERR_UNSUPPORTED;
+    }
+    p->ball_kmax = kmax;
+    const size_t nW = W.size(), oK = align_up(rs * nW);
+    if (e == cudaSuccess) e = cudaMalloc(&p->ball_W, oK + sizeof(int) * counts.size());
+    if (e == cudaSuccess) {
+      p->ball_K = (int *)((char *)p->ball_W + oK);
+      std::vector<float> Wf(W.begin(), W.end());
+      e = cudaMemcpy(p->ball_W, p->fp64 ? (const void *)W.data() : (const void *)Wf.data(), rs * nW,
+                     cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p->ball_K, counts.data(), sizeof(int) * counts.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+      if (p->ball_W) cudaFree(p->ball_W);
+      cudaFree(p->base);
+      delete p;
+      return fail_cuda(e, "plan ball tables");
+    }
+  }
   *out = reinterpret_cast<matcha_plan>(p);
   return MATCHA_OK;
 }
@@ -227,6 +278,7 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
     if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ball_W) cudaFree(p->ball_W);
   cudaError_t e = cudaFree(p->base);
   delete p;
   if (e != cudaSuccess) return fail_cuda(e, "cudaFree(plan tables)");
@@ -341,6 +393,21 @@ matcha_status matcha_newton_march(matcha_plan plan, const void *c, int B, const 
                           : launch_newton<float>(*p, (const float *)c, B, n_cand, euler, score,
                                                  cflags, work, st);
   if (e != cudaSuccess) return fail_cuda(e, "newton_march");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_objective(matcha_plan plan, const void *c, int B, int L, int Q,
+                               const double *euler, double *out, void *stream) {
+  if (!plan || B < 0 || Q < 0) return MATCHA_ERR_INVALID_ARG;
+  if (B == 0 || Q == 0) return MATCHA_OK;
+  if (!c || !euler || !out) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  if (Q > p->P || L < 0 || L > p->LJ) return MATCHA_ERR_INVALID_ARG;
+  if (B > 65535) return MATCHA_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p->fp64 ? launch_objective<double>(*p, (const double *)c, B, L, Q, euler, out, st)
+                          : launch_objective<float>(*p, (const float *)c, B, L, Q, euler, out, st);
+  if (e != cudaSuccess) return fail_cuda(e, "objective");
   return MATCHA_OK;
 }
 
@@ -680,6 +747,15 @@ matcha_status matcha_template_grad(matcha_plan plan, const void *f, const void *
   Plan *p = P_(plan);
   if (!backward_fits(*p)) {
     set_error_text("template gradient: the per-degree tables of this bandwidth exceed shared memory");
+    return MATCHA_ERR_UNSUPPORTED;
+  }
+  if (p->ball_kmax > 0) {
+    set_error_text("template gradient: not available with the ball-harmonic radial basis");
+    return MATCHA_ERR_UNSUPPORTED;
+  }
+  if (!p->fp64 && p->LJ > 64) {
+    set_error_text("template gradient: the 32-bit gradient recurrences are not rescaled; "
+                   "L_J <= 64 (use an FP64 plan above)");
     return MATCHA_ERR_UNSUPPORTED;
   }
   double *shift;

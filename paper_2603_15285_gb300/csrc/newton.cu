@@ -215,6 +215,91 @@ __device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, unsigned z,
   }
 }
 
+// 2^e as a float for -126 <= e <= 127, 0 below (values that small times a
+// state below 2^32 are far under FP32 resolution of any sum they enter).
+__device__ __forceinline__ float pow2f(int e) {
+  return e < -126 ? 0.f : __int_as_float((min(e, 127) + 127) << 23);
+}
+
+// Extended-range power x^k = mant 2^expo (mant in [0.5, 1), or 0 for x = 0,
+// k > 0) by binary powering with the exponent carried as an integer, so
+// that powers far below the FP32 range keep their leading bits.
+__device__ __forceinline__ void xpow(float x, int k, float &mant, int &expo) {
+  int ex;
+  float xm = frexpf(x, &ex);
+  float rm = 1.f;
+  int re = 0;
+  while (k) {
+    if (k & 1) {
+      int t;
+      rm = frexpf(rm * xm, &t);
+      re += ex + t;
+    }
+    k >>= 1;
+    if (k) {
+      int t;
+      xm = frexpf(xm * xm, &t);
+      ex = 2 * ex + t;
+    }
+  }
+  if (rm == 0.f) re = 0;
+  int t;
+  mant = frexpf(rm, &t);
+  expo = re + t;
+}
+
+// Seeds of the rescaled recurrence (32-bit plans above L_J = 64).  The
+// powers come as (mantissa, exponent) from the extended-range tables: pc,
+// ps address ch^aa and sh^ba, pe is the byte offset of the exponent rows.
+// The states D0, D1, D2 of half h are the true seeds divided by 2^E_h,
+// E_h = the exponent of K ch^a sh^b, so the state of d starts near 1 however
+// small the true seed is; D1 and D2 keep their ratio to D0.
+template <bool FULL>
+__device__ __forceinline__ void group_seed_rs(unsigned pc, unsigned ps, unsigned pe, unsigned z,
+                                              v2<float> K, int aa, int ba, v2<float> &D0,
+                                              v2<float> &D1, v2<float> &D2, int &E0, int &E1) {
+  auto ldm = [&](unsigned a, float &m, int &e) {
+    float ef;
+    lds1(a, m);
+    lds1(a + pe, ef);
+    e = (int)ef;
+  };
+  float c0, c1, s0, sm1;
+  int ec0, ec1, es0, esm1;
+  ldm(pc, c0, ec0); ldm(pc + z, c1, ec1);
+  ldm(ps, s0, es0); ldm(ps - z, sm1, esm1);
+  int kex, key;
+  const float kmx = frexpf(K.x, &kex), kmy = frexpf(K.y, &key);
+  const int R0 = ec0 + es0, R1 = ec1 + esm1;  // reference exponents of ch^a sh^b
+  E0 = kex + R0;
+  E1 = key + R1;
+  const float g0 = kmx, g1 = -kmy;            // sigma K of both halves, mantissas
+  D0 = vset<float>(g0 * c0 * s0, g1 * c1 * sm1);
+  if (FULL) {
+    float c2, c3, cm1, cm2, s1, s2, sm2, sm3;
+    int ec2, ec3, ecm1, ecm2, es1, es2, esm2, esm3;
+    ldm(pc + 2 * z, c2, ec2); ldm(pc + 3 * z, c3, ec3);
+    ldm(pc - z, cm1, ecm1); ldm(pc - 2 * z, cm2, ecm2);
+    ldm(ps + z, s1, es1); ldm(ps + 2 * z, s2, es2);
+    ldm(ps - 2 * z, sm2, esm2); ldm(ps - 3 * z, sm3, esm3);
+    // ch^i sh^j relative to 2^R
+    auto rel = [](float cm, int ce, float sm, int se, int R) { return cm * sm * pow2f(ce + se - R); };
+    const float fa = (float)aa, fb = (float)ba;
+    // half 0: a = aa, b = ba; half 1: a = aa + 1, b = ba - 1
+    const float t1a = fb * rel(c1, ec1, sm1, esm1, R0), t2a = fa * rel(cm1, ecm1, s1, es1, R0);
+    const float t1b = (fb - 1.f) * rel(c2, ec2, sm2, esm2, R1), t2b = (fa + 1.f) * rel(c0, ec0, s0, es0, R1);
+    D1 = vset<float>(0.5f * g0 * (t1a - t2a), 0.5f * g1 * (t1b - t2b));
+    const float A0 = fa, B0 = fb, A1 = fa + 1.f, B1 = fb - 1.f;
+    const float u1a = B0 * (B0 - 1.f) * rel(c2, ec2, sm2, esm2, R0);
+    const float u2a = (B0 * (A0 + 1.f) + A0 * (B0 + 1.f)) * rel(c0, ec0, s0, es0, R0);
+    const float u3a = A0 * (A0 - 1.f) * rel(cm2, ecm2, s2, es2, R0);
+    const float u1b = B1 * (B1 - 1.f) * rel(c3, ec3, sm3, esm3, R1);
+    const float u2b = (B1 * (A1 + 1.f) + A1 * (B1 + 1.f)) * rel(c1, ec1, sm1, esm1, R1);
+    const float u3b = A1 * (A1 - 1.f) * rel(cm1, ecm1, s1, es1, R1);
+    D2 = vset<float>(0.25f * g0 * (u1a + u3a - u2a), 0.25f * g1 * (u1b + u3b - u2b));
+  }
+}
+
 // One staged degree entry of a partner group: c of both halves, and the
 // recurrence coefficients (a, -b, -e) of the step to the next degree.
 template <typename T> struct Coef {
@@ -301,6 +386,56 @@ __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> N
   }
 }
 
+// group_sum for the rescaled states of group_seed_rs: the true d, d', d'' of
+// half h are the states times 2^E_h.  Each accumulation multiplies the state
+// by SC = 2^E (0 while the true values are below 2^-126); after each step a
+// half whose state has grown past 2^32 while E_h < 0 is scaled down by 2^32
+// (exactly) and E_h raised by 32, so the states neither overflow nor lose the
+// digits of seeds far below the FP32 range (per-degree rescaling).
+__device__ __forceinline__ void rescale_half(float &p0, float &p1, float &p2, float &d0, float &d1,
+                                             float &d2, int &E, float &sc) {
+  if (E < 0 && fabsf(p0) > 4294967296.f) {
+    const float f = 2.3283064365386963e-10f;  // 2^-32
+    p0 *= f; p1 *= f; p2 *= f; d0 *= f; d1 *= f; d2 *= f;
+    E += 32;
+    sc = pow2f(E);
+  }
+}
+
+template <bool FULL>
+__device__ __forceinline__ void group_sum_rs(unsigned a, int last, v2<float> X, v2<float> NS,
+                                             v2<float> NX, v2<float> D0, v2<float> D1, v2<float> D2,
+                                             int E0, int E1, v2<float> (&Z)[12]) {
+  constexpr unsigned ES = 16 * sizeof(float);
+  const v2<float> zero = vset<float>(0.f, 0.f);
+  v2<float> P0 = zero, P1 = zero, P2 = zero;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) Z[q] = zero;
+  float scx = pow2f(E0), scy = pow2f(E1);
+  Coef<float> e;
+  Rec<float> r;
+  auto acc = [&](const v2<float> &S0, const v2<float> &S1, const v2<float> &S2) {
+    const v2<float> SC = vset<float>(scx, scy);
+    accumulate<float, FULL>(e, vmul(S0, SC), vmul(S1, SC), vmul(S2, SC), Z);
+  };
+  for (int i = 0; i <= last; ++i, a += ES) {
+    load_coef(a, e);
+    if (i & 1) acc(P0, P1, P2);
+    else acc(D0, D1, D2);
+    if (i == last) break;
+    load_rec(a, r);
+    if (i & 1) {
+      step_into<float, FULL>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
+      rescale_half(D0.x, D1.x, D2.x, P0.x, P1.x, P2.x, E0, scx);
+      rescale_half(D0.y, D1.y, D2.y, P0.y, P1.y, P2.y, E1, scy);
+    } else {
+      step_into<float, FULL>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+      rescale_half(P0.x, P1.x, P2.x, D0.x, D1.x, D2.x, E0, scx);
+      rescale_half(P0.y, P1.y, P2.y, D0.y, D1.y, D2.y, E1, scy);
+    }
+  }
+}
+
 // Adds one image of both halves to the candidate's sums.  The image has phase
 // E = e^{i(u a + v g)} and weight W; (zr0, zi0) = S0 E, (zr1, zi1) = S1 E,
 // zr2 = Re S2 E for the d, d', d'' sums S0, S1, S2.  d/da brings i u and d/dg
@@ -354,7 +489,7 @@ __device__ __forceinline__ void phase(v2<T> Ar, v2<T> Ai, v2<T> Gr, v2<T> Gi, v2
 // g = slot, slot + nslots, ... of bandwidth L; the next group's entries are
 // copied into the other half of the slot's buffer while the current one is
 // summed, so every shared-memory read in the l-loop is a broadcast.
-template <typename T, bool FULL>
+template <typename T, bool FULL, bool RS>
 __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
                                          const T *__restrict__ rcoef, const T *__restrict__ seedK,
                                          const double *pts, const int *need, SmemLayout &sm) {
@@ -379,7 +514,16 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   for (int t = tid; t < 2 * P * npk; t += blockDim.x) {
     int pr = dw.div(t), k = t - pr * npk;
     int p = pr >> 1, which = pr & 1;
-    if (need[p]) pw[(which * NPW + PW_PAD + k) * PS + p] = ipow_t(evp[8 * p + 2 + which], k);
+    if (!need[p]) continue;
+    if (RS) {  // mantissa rows, then exponent rows (2 NPW rows further on)
+      float mt;
+      int ex;
+      xpow((float)evp[8 * p + 2 + which], k, mt, ex);
+      pw[(which * NPW + PW_PAD + k) * PS + p] = (T)mt;
+      pw[((2 + which) * NPW + PW_PAD + k) * PS + p] = (T)ex;
+    } else {
+      pw[(which * NPW + PW_PAD + k) * PS + p] = ipow_t(evp[8 * p + 2 + which], k);
+    }
   }
   if (tid < 2 * P) {
     int p = tid >> 1, which = tid & 1;
@@ -466,8 +610,15 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
         v2<T> K, D0, D1, D2, Z[12];
         lds2(buf, K);
         D1 = D2 = vset<T>(T(0), T(0));
-        group_seed<T, FULL>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
-        group_sum<T, FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+        if constexpr (RS) {
+          int E0, E1;
+          group_seed_rs<FULL>(pcu + zs * aa, psu + zs * ba, zs * 2 * NPW, zs, K, aa, ba, D0, D1,
+                              D2, E0, E1);
+          group_sum_rs<FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, E0, E1, Z);
+        } else {
+          group_seed<T, FULL>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
+          group_sum<T, FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+        }
         const T fm = T(m), fa = T(na);
         const v2<T> MM = vset<T>(fm, fm), NN = vset<T>(fa, fa + T(1));
         // image (m, n): phase e^{i(m a + n g)}, weight 1 for (0, 0) else 2
@@ -638,16 +789,9 @@ __device__ __forceinline__ void start_step(int tid, int L, const NewtonArgs &A, 
   sm.state[tid] = ST_TRIAL;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
-k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
-         const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
-         double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
-         long long *__restrict__ work) {
-  const long b = blockIdx.x;
-  const int P = A.P, tid = threadIdx.x;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemLayout sm;
+// Carves the refinement kernels' shared memory (layout of newton_smem_bytes).
+template <typename T, bool RS>
+__device__ __forceinline__ int *carve_smem(unsigned char *smem_raw, int P, int LJ, SmemLayout &sm) {
   double *dp = reinterpret_cast<double *>(smem_raw);
   sm.th = dp; dp += 3 * P;
   sm.tr = dp; dp += 3 * P;
@@ -665,14 +809,49 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
   T *tp = reinterpret_cast<T *>(u);
   sm.red = tp; tp += 10 * P * NEWTON_WARPS;
   sm.evp = tp; tp += 8 * P;
-  sm.ea = tp; tp += 4 * cand_stride(P) * ph_row(A.LJ);  // phase rows
-  sm.pw = tp; tp += 2 * cand_stride(P) * pw_row(A.LJ);
+  sm.ea = tp; tp += 4 * cand_stride(P) * ph_row(LJ);
+  sm.pw = tp; tp += (RS ? 4 : 2) * cand_stride(P) * pw_row(LJ);
   tp = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(tp) + 31) & ~uintptr_t(31));
-  sm.stage = tp;  // [slots][2][stage_half(L_J)]
-
-  const int nc_b = n_cand[b];
-  for (int t = tid; t < 2 * cand_stride(P) * pw_row(A.LJ); t += blockDim.x)
+  sm.stage = tp;
+  for (int t = threadIdx.x; t < (RS ? 4 : 2) * cand_stride(P) * pw_row(LJ); t += blockDim.x)
     ((T *)sm.pw)[t] = T(0);  // pads
+  return need;
+}
+
+// C_L, its gradient and Hessian (Section 2.2) at Q given rotations per
+// particle: the refinement kernel's evaluation, one CTA per particle.
+// out[b][q][10] = (C, C_a, C_b, C_g, C_aa, C_ab, C_ag, C_bb, C_bg, C_gg).
+template <typename T, bool RS>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_objective(const T *__restrict__ c, const T *__restrict__ rcoef, const T *__restrict__ seedK,
+            NewtonArgs A, int L, int Q, const double *__restrict__ pts, double *__restrict__ out) {
+  const long b = blockIdx.x;
+  const int tid = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemLayout sm;
+  int *need = carve_smem<T, RS>(smem_raw, A.P, A.LJ, sm);
+  if (tid < A.P) {
+    const bool on = tid < Q;
+    for (int i = 0; i < 3; ++i) sm.th[3 * tid + i] = on ? pts[3 * (b * Q + tid) + i] : 0.0;
+    need[tid] = on;
+  }
+  __syncthreads();
+  evaluate<T, true, RS>(A, L, c + 4 * b * A.nc, rcoef, seedK, sm.th, need, sm);
+  for (int t = tid; t < Q * 10; t += blockDim.x) out[10 * b * Q + t] = sm.res[t];
+}
+
+template <typename T, bool RS>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
+         const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
+         double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
+         long long *__restrict__ work) {
+  const long b = blockIdx.x;
+  const int P = A.P, tid = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemLayout sm;  // staging buffers: [slots][2][stage_half(L_J)]
+  int *need = carve_smem<T, RS>(smem_raw, P, A.LJ, sm);
+  const int nc_b = n_cand[b];
   if (tid < P) {
     double *e = euler + 3 * (b * P + tid);
     sm.th[3 * tid] = e[0]; sm.th[3 * tid + 1] = e[1]; sm.th[3 * tid + 2] = e[2];
@@ -700,7 +879,7 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
     if (!__syncthreads_or(want)) break;
     if (tid == 0)
       for (int q = 0; q < P; ++q) work_full += need[q] ? steps_L : 0;
-    evaluate<T, true>(A, L, cb, rcoef, seedK, sm.th, need, sm);
+    evaluate<T, true, RS>(A, L, cb, rcoef, seedK, sm.th, need, sm);
     // the 3x3 solves of the final level run in FP64 in every plan
     const bool last = lev == A.nlev - 1;
     auto step_from = [&]() {
@@ -722,8 +901,8 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
       const bool full = __syncthreads_or(wf);
       if (tid == 0)
         for (int q = 0; q < P; ++q) (full ? work_full : work_val) += need[q] ? steps_L : 0;
-      if (full) evaluate<T, true>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
-      else evaluate<T, false>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
+      if (full) evaluate<T, true, RS>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
+      else evaluate<T, false, RS>(A, L, cb, rcoef, seedK, sm.tr, need, sm);
       if (tid < P && need[tid]) {
         double Ct = sm.res[10 * tid];
         if (Ct >= sm.Cc[tid] - A.acc_tol * fabs(sm.Cc[tid])) {
@@ -771,13 +950,20 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
 static int newton_cpw(int P) { return P <= 16 ? 16 : 32; }
 
 // Shared memory of k_newton with `slots` staging buffers.
+// Above this bandwidth the 32-bit plans run the rescaled recurrence: seeds
+// flushed below the FP32 range would otherwise grow into significant terms
+// (at L_J = 100 a seed under 2^-126 reaches 2.6e-4).
+constexpr int RESCALE_ABOVE_L = 64;
+static bool newton_rescaled(const Plan &p, size_t tsize) { return tsize == 4 && p.LJ > RESCALE_ABOVE_L; }
+
 static size_t newton_smem_bytes(const Plan &p, size_t tsize, int slots) {
   size_t P = p.P;
+  const size_t pw_rows = newton_rescaled(p, tsize) ? 4 : 2;
   size_t bytes = sizeof(double) * (3 * P * 3 + P + 10 * P);
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
   const size_t PS = cand_stride(p.P);
-  bytes += tsize * (10 * P * NEWTON_WARPS + 8 * P + 4 * PS * ph_row(p.LJ) + 2 * PS * pw_row(p.LJ)) + 32;
+  bytes += tsize * (10 * P * NEWTON_WARPS + 8 * P + 4 * PS * ph_row(p.LJ) + pw_rows * PS * pw_row(p.LJ)) + 32;
   bytes += tsize * (size_t)slots * 2 * stage_half(p.LJ);
   return bytes;
 }
@@ -808,11 +994,49 @@ cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, d
   A.grad = p.refine;
   A.nc = p.nc;
   size_t smem = newton_smem_bytes(p, sizeof(T), A.nslots);
-  cudaFuncSetAttribute(k_newton<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_newton<T><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK, A,
-                                               n_cand, euler, score, cflags, work);
+  if constexpr (sizeof(T) == 4) {
+    if (newton_rescaled(p, sizeof(T))) {
+      cudaFuncSetAttribute(k_newton<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_newton<T, true><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK,
+                                                         A, n_cand, euler, score, cflags, work);
+      return cudaGetLastError();
+    }
+  }
+  cudaFuncSetAttribute(k_newton<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_newton<T, false><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK,
+                                                      A, n_cand, euler, score, cflags, work);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_objective(const Plan &p, const T *c, int B, int L, int Q, const double *pts,
+                             double *out, cudaStream_t st) {
+  if (B == 0 || Q == 0) return cudaSuccess;
+  NewtonArgs A;
+  A.LJ = p.LJ; A.nlev = p.nlev; A.M = p.M; A.P = p.P;
+  A.cpw = newton_cpw(p.P);
+  A.nslots = newton_slots(p, sizeof(T));
+  if (A.nslots == 0) return cudaErrorInvalidConfiguration;
+  for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
+  A.tol = p.step_tol; A.acc_tol = p.accept_tol; A.grad = p.refine; A.nc = p.nc;
+  size_t smem = newton_smem_bytes(p, sizeof(T), A.nslots);
+  if constexpr (sizeof(T) == 4) {
+    if (newton_rescaled(p, sizeof(T))) {
+      cudaFuncSetAttribute(k_objective<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_objective<T, true><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef,
+                                                            (const T *)p.seedK, A, L, Q, pts, out);
+      return cudaGetLastError();
+    }
+  }
+  cudaFuncSetAttribute(k_objective<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_objective<T, false><<<B, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK,
+                                                         A, L, Q, pts, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_objective<float>(const Plan &, const float *, int, int, int,
+                                             const double *, double *, cudaStream_t);
+template cudaError_t launch_objective<double>(const Plan &, const double *, int, int, int,
+                                              const double *, double *, cudaStream_t);
 
 template cudaError_t launch_newton<float>(const Plan &, const float *, int, const int *, double *,
                                           double *, int *, long long *, cudaStream_t);

@@ -972,6 +972,14 @@ bool soft_grid_optional(const Plan &p) {
          (!p.fp64 && soft_fused_ok(p));
 }
 
+// True when one of the SOFFT kernels serves the plan (the grid kernel's
+// per-slice tables grow with the points per angle).
+bool soft_fits(const Plan &p) {
+  if (soft_grid_optional(p)) return true;
+  const size_t ts = p.fp64 ? 8 : 4, W = 2 * p.L0 + 1;
+  return ts * (2 * W * W + 2 * (size_t)(p.L0 + 1) * p.ns) <= 227 * 1024 - 1024;
+}
+
 template <typename T>
 cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
                         double *euler, double *score, int *n_cand, cudaStream_t st) {

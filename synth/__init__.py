@@ -118,6 +118,18 @@ WORKLOADS = {
     "paper200": Workload("paper200", B=256, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,
                          snr=1.0, wedge_deg=60.0, n_shells=40, L_sched=(30, 40),
                          L0=30, K=2, P=10, M_iter=1, base_seed=20260321),
+    # Bandwidths above 64 (up to the paper's L_max <= 100): a 64^3 pair marched to
+    # L = 100, and the paper's own schedules at 200^3: {30, 40, 60, 100} with one
+    # Newton step per band, and M_iter = 5 over {30, 40, 45} (its STA setting).
+    "wide64": Workload("wide64", B=2, N=64, n_blobs=48, sigma=2.0, ball_radius=26.0,
+                       snr=0.1, wedge_deg=60.0, n_shells=32, L_sched=(8, 16, 32, 64, 100),
+                       L0=8, K=2, P=8, M_iter=3, base_seed=20260325),
+    "paper200w": Workload("paper200w", B=4, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,
+                          snr=1.0, wedge_deg=60.0, n_shells=40, L_sched=(30, 40, 60, 100),
+                          L0=30, K=2, P=10, M_iter=1, base_seed=20260321),
+    "sta200": Workload("sta200", B=4, N=200, n_blobs=160, sigma=3.0, ball_radius=80.0,
+                       snr=1.0, wedge_deg=60.0, n_shells=40, L_sched=(30, 40, 45),
+                       L0=30, K=2, P=10, M_iter=5, base_seed=20260321),
     # 6-D pose (rotation and translation): planted shifts up to 3 voxels, three
     # rotation-translation alternations, integer search window +-5 voxels.
     "shift32": Workload("shift32", B=2, N=32, n_blobs=16, sigma=1.5, ball_radius=10.0,

@@ -55,9 +55,9 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(box_n=2), dict(n_shells=0), dict(L0=0), dict(K_oversample=9), dict(P_max=0),
+    dict(box_n=2), dict(n_shells=0), dict(L0=0), dict(K_oversample=17), dict(P_max=0),
     dict(P_max=33), dict(M_iter=0), dict(precision=7), dict(L_sched=(8, 8, 16)),
-    dict(L_sched=(4, 12, 16)), dict(r_max=float("nan")),
+    dict(L_sched=(4, 12, 16)), dict(r_max=float("nan")), dict(refine=2),
 ])
 def test_plan_create_rejects_bad_descriptors_on_host(L, bad):
     d = _desc(**bad)
@@ -67,7 +67,7 @@ def test_plan_create_rejects_bad_descriptors_on_host(L, bad):
 
 
 def test_bandwidth_limit_is_unsupported_not_a_crash(L):
-    d = _desc(L_sched=(8, 40, 80))
+    d = _desc(L_sched=(8, 40, 120))
     h = ctypes.c_void_p()
     assert L.matcha_plan_create(ctypes.byref(d), ctypes.byref(h)) == 5
 
