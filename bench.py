@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-oracle-gate", action="store_true",
                     help="skip the oracle run over the whole batch (accuracy against the oracle)")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
+    ap.add_argument("--paper-batch", type=int, default=256, help="particles of the 200^3 leg")
+    ap.add_argument("--pose6d-batch", type=int, default=1024, help="particles of the 6-D leg")
     return ap.parse_args()
 
 
@@ -277,7 +279,8 @@ def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
     T0 = (w.L0 + 1) * (2 * w.L0 + 1) * (2 * w.L0 + 3) // 3
     soft_flops = (4.0 * n * T0 + 2.5 * n ** 3 * math.log2(n * n)) * B
     sp = alu_peak
-    out["soft"] = {"kernel": "k_soft_chunk", "bound": "alu", "unit": "TFLOP/s", "peak": sp,
+    out["soft"] = {"kernel": "k_soft_chunk", "bound": "alu",
+                   "unit": "TFLOP/s", "peak": sp,
                    "flops_per_particle": soft_flops / B,
                    "achieved": soft_flops / (stage_ms["soft"] * 1e-3) / 1e12,
                    "grid_points_per_s": n ** 3 * B / (stage_ms["soft"] * 1e-3)}
@@ -358,10 +361,13 @@ def time_mixed(st, prec, reps=5):
             "particles": total, "ms_per_step": ms, "value": total / (ms * 1e-3),
             "unit": "particles/s", "timed": "one CUDA graph of all groups, replayed",
             "autotune": [{"shells_per_analysis_cta": t["analyze_shells"],
-                          "tc_ctas_per_sm": t["tc_ctas_per_sm"]} for t in mb.tune]}
+                          "tc_ctas_per_sm": t["tc_ctas_per_sm"],
+                          "soft_kernel": t.get("soft_kernel", 0),
+                          "newton_sched": t.get("newton_sched", 0),
+                          "newton_ms": t.get("newton_ms")} for t in mb.tune]}
 
 
-def time_paper_scale(st, reps=3):
+def time_paper_scale(st, reps=3, n=256):
     """The paper's own regime (200^3 boxes, 40 shells, SOFFT at L0 = 30 with
     K = 2, P = 10, one Newton step per band, L 30 -> 40, 0 dB): FP32 and FP64
     plans, eager matcha_align, errors against FP64 and the planted rotation."""
@@ -371,7 +377,7 @@ def time_paper_scale(st, reps=3):
     import paper_2603_15285_gb300 as m
     import synth
     w = synth.WORKLOADS["paper200"]
-    d = synth.make_batch(w, device="cuda")
+    d = synth.make_batch(w, B=n, device="cuda")
     parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
     B = parts.shape[0]
     out = {"workload": "paper200: %d particles of 200^3, 40 shells, L0=30 K=2 (124^3 grid), P=10, "
@@ -401,7 +407,7 @@ def time_paper_scale(st, reps=3):
     return out
 
 
-def time_pose6d(st, reps=3):
+def time_pose6d(st, reps=3, n=None):
     """6-D pose (rotation and translation) on the 1024-particle 64^3 batch with
     planted shifts up to 3 voxels: three rotation-translation alternations
     (matcha_align6d: per round the rotation search, the rotated template, the
@@ -412,7 +418,7 @@ def time_pose6d(st, reps=3):
     import paper_2603_15285_gb300 as m
     import synth
     w = synth.WORKLOADS["shift64"]
-    d = synth.make_batch(w, device="cuda")
+    d = synth.make_batch(w, B=n, device="cuda")
     parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
     B = parts.shape[0]
     plan = m.plan_for_workload(w, precision=m.FP32)
@@ -863,11 +869,11 @@ def main():
         import torch
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_pose6d:
-        res["pose6d"] = time_pose6d(st)
+        res["pose6d"] = time_pose6d(st, n=args.pose6d_batch)
         import torch
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_paper:
-        res["paper_scale"] = time_paper_scale(st)
+        res["paper_scale"] = time_paper_scale(st, n=args.paper_batch)
         import torch
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:

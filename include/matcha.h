@@ -284,21 +284,37 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
 
 /* Autotuning.  Times, on the given batch, the tile choices that leave every
  * result bit unchanged and keeps the fastest in the plan: the shells per
- * analysis CTA (1, 2, 4 or 8, those whose shared memory fits) and, for TF32 /
- * BF16 plans, the tensor-core contraction's CTAs per SM (1 or 2).  Uses the
- * matcha_align workspace for its scratch; synchronises `stream` (not
- * graph-capturable: tune first, then capture).  report: the choices and the
- * best time (ms) of each candidate, -1 where a candidate does not apply. */
+ * analysis CTA (1, 2, 4 or 8, those whose shared memory fits), for TF32 /
+ * BF16 plans the tensor-core contraction's CTAs per SM (1 or 2), and for
+ * 32-bit plans whose grid fits it the SOFFT search kernel (1: the chunked
+ * kernels, 2: one warp per beta slice), and the refinement schedule of
+ * matcha_align (1: one CTA per particle, 2: persistent CTAs on a cost-sorted
+ * queue, longest processing time first).  P_per_dev (nullable) gives the
+ * per-particle candidate counts as for matcha_align.  Uses the matcha_align workspace for
+ * its scratch; synchronises `stream` (not graph-capturable: tune first, then
+ * capture).  report: the choices and the best time (ms) of each candidate,
+ * -1 where a candidate does not apply. */
 typedef struct {
   int analyze_shells;
   float analyze_ms[4];     /* candidates 1, 2, 4, 8 shells per CTA */
   int tc_ctas_per_sm;      /* 0 when the plan's contraction runs on the CUDA cores */
   float tc_ms[2];          /* candidates 1, 2 CTAs per SM */
+  int soft_kernel;         /* 0 when only one SOFFT kernel serves the plan */
+  float soft_ms[2];        /* candidates 1 (chunked), 2 (warp per slice) */
+  int newton_sched;        /* matcha_align's refinement: 1 a CTA per particle in index
+                              order, 2 persistent CTAs pulling particles from a queue
+                              sorted by decreasing candidate count */
+  float newton_ms[2];
 } matcha_tune_report;
 matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles_dev,
                                    const float *templates_dev, int B, int template_batch_stride,
-                                   void *ws_dev, size_t ws_bytes, void *stream,
-                                   matcha_tune_report *report);
+                                   const int *P_per_dev, void *ws_dev, size_t ws_bytes,
+                                   void *stream, matcha_tune_report *report);
+/* Sets the plan's tile choices directly (the choice fields of a report:
+ * analyze_shells, tc_ctas_per_sm, soft_kernel, newton_sched; 0 restores the
+ * built-in rule for that field).  Every choice gives bit-identical results; invalid values
+ * return MATCHA_ERR_INVALID_ARG and change nothing. */
+matcha_status matcha_plan_set_tiles(matcha_plan plan, const matcha_tune_report *choices);
 
 /* Gradient of the refined scores with respect to the template.
  *

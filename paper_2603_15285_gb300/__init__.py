@@ -32,6 +32,7 @@ SYMBOLS = [
     "matcha_plan_device_status", "matcha_plan_autotune", "matcha_plan_set_wait_limit",
     "matcha_transform_volumes", "matcha_shift_search_workspace_size", "matcha_shift_search",
     "matcha_align6d_workspace_size", "matcha_align6d", "matcha_objective",
+    "matcha_plan_set_tiles",
 ]
 
 
@@ -56,7 +57,9 @@ class PlanInfo(ctypes.Structure):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("analyze_shells", ctypes.c_int), ("analyze_ms", ctypes.c_float * 4),
-                ("tc_ctas_per_sm", ctypes.c_int), ("tc_ms", ctypes.c_float * 2)]
+                ("tc_ctas_per_sm", ctypes.c_int), ("tc_ms", ctypes.c_float * 2),
+                ("soft_kernel", ctypes.c_int), ("soft_ms", ctypes.c_float * 2),
+                ("newton_sched", ctypes.c_int), ("newton_ms", ctypes.c_float * 2)]
 
 
 _lib = None
@@ -89,10 +92,11 @@ def lib():
             "matcha_template_grad_workspace_size": [_vp, i, i, ctypes.POINTER(sz)],
             "matcha_plan_device_status": [_vp, ctypes.POINTER(i)],
             "matcha_plan_set_wait_limit": [_vp, l],
-            "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
+            "matcha_plan_autotune": [_vp, _vp, _vp, i, i, _vp, _vp, sz, _vp, ctypes.POINTER(TuneReport)],
             "matcha_template_grad": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_transform_volumes": [i, _vp, i, i, _vp, _vp, i, _vp, _vp],
             "matcha_objective": [_vp, _vp, i, i, i, _vp, _vp, _vp],
+            "matcha_plan_set_tiles": [_vp, ctypes.POINTER(TuneReport)],
             "matcha_shift_search_workspace_size": [_vp, i, i, i, ctypes.POINTER(sz)],
             "matcha_shift_search": [_vp, _vp, _vp, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, sz, _vp],
             "matcha_align6d_workspace_size": [_vp, i, i, i, i, ctypes.POINTER(sz)],
@@ -195,7 +199,7 @@ class Plan:
                "matcha_plan_table")
         return out
 
-    def autotune(self, particles, templates, ws=None) -> dict:
+    def autotune(self, particles, templates, ws=None, P_per=None) -> dict:
         """Times the result-invariant tile choices on this batch and keeps the
         fastest in the plan (``matcha_plan_autotune``); returns the report."""
         torch = _torch()
@@ -207,11 +211,23 @@ class Plan:
         base = ws.data_ptr()
         aligned = (base + 255) // 256 * 256
         rep = TuneReport()
+        if P_per is not None:
+            _need(P_per, torch.int32, "P_per")
         _check(lib().matcha_plan_autotune(self.handle, _ptr(particles), _ptr(templates), B, stride,
-                                          aligned, ws.numel() - (aligned - base), _stream(),
-                                          ctypes.byref(rep)), "matcha_plan_autotune")
+                                          _ptr(P_per), aligned, ws.numel() - (aligned - base),
+                                          _stream(), ctypes.byref(rep)), "matcha_plan_autotune")
         return dict(analyze_shells=rep.analyze_shells, analyze_ms=list(rep.analyze_ms),
-                    tc_ctas_per_sm=rep.tc_ctas_per_sm, tc_ms=list(rep.tc_ms))
+                    tc_ctas_per_sm=rep.tc_ctas_per_sm, tc_ms=list(rep.tc_ms),
+                    soft_kernel=rep.soft_kernel, soft_ms=list(rep.soft_ms),
+                    newton_sched=rep.newton_sched, newton_ms=list(rep.newton_ms))
+
+    def set_tiles(self, analyze_shells: int = 0, tc_ctas_per_sm: int = 0, soft_kernel: int = 0,
+                  newton_sched: int = 0):
+        """Pins the result-invariant tile choices (0: the built-in rule)."""
+        rep = TuneReport()
+        rep.analyze_shells, rep.tc_ctas_per_sm, rep.soft_kernel = analyze_shells, tc_ctas_per_sm, soft_kernel
+        rep.newton_sched = newton_sched
+        _check(lib().matcha_plan_set_tiles(self.handle, ctypes.byref(rep)), "matcha_plan_set_tiles")
 
     def set_wait_limit(self, polls: int):
         """Polls before a tensor-core wait gives up (-1: built-in; 0: at once, for tests)."""

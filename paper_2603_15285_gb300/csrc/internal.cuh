@@ -24,6 +24,8 @@ struct Plan {
   // them changes any result bit
   int tune_shells = 0;   // shells per analysis CTA (1, 2, 4, 8)
   int tune_tc_ctas = 0;  // tensor-core contraction CTAs per SM (1, 2)
+  int tune_soft = 0;     // SOFFT search kernel: 1 the chunked kernels, 2 warp per slice
+  int tune_newton = 0;   // refinement schedule: 1 a CTA per particle, 2 persistent cost-sorted queue
   long wait_limit = -1;  // mbarrier polls before a wait gives up (-1: the built-in limit)
   int nt, np, nlm, npairs, npairs0, ns;
   int ngroups;  // partner groups of the correlation layout, (L_J+1)(L_J+2)/2
@@ -115,6 +117,10 @@ template <typename T>
 cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
                           double *score, int *cflags, long long *work, cudaStream_t st);
 template <typename T>
+cudaError_t launch_newton_queue(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
+                                double *score, int *cflags, long long *work, int *order,
+                                int *ticket, cudaStream_t st);
+template <typename T>
 cudaError_t launch_objective(const Plan &p, const T *c, int B, int L, int Q, const double *pts,
                              double *out, cudaStream_t st);
 template <typename T>
@@ -129,6 +135,7 @@ bool newton_fits(const Plan &p);  // the refinement kernel's shared memory fits
 bool analyze_shells_ok(const Plan &p, int G);  // G shells per analysis CTA fit
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
 bool soft_fits(const Plan &p);           // some SOFFT kernel serves the plan
+bool soft_warps_ok(const Plan &p);       // the warp-per-slice SOFFT kernel serves the plan
 // Translation search (translate.cu): volume poses, the box FFT, the cross
 // spectrum and the windowed inverse DFT of the correlation.
 cudaError_t launch_pose_volumes(int N, const float *vol, int B, long vol_stride, const double *R,

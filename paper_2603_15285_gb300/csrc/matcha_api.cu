@@ -51,6 +51,8 @@ struct AlignWs {
   void *f, *h, *c, *grid;
   int *cidx, *cflags, *ncand;
   double *ceuler, *cscore;
+  int *order, *ticket;  // the cost-sorted Newton queue (one ticket per part start)
+  double *ceuler0;      // the autotuner's copy of the refinement's start points
 };
 
 size_t carve_align(const Plan &p, int B, int Bt, char *base, AlignWs *w) {
@@ -67,6 +69,9 @@ size_t carve_align(const Plan &p, int B, int Bt, char *base, AlignWs *w) {
   w->ncand = cv.take<int>(B);
   w->ceuler = cv.take<double>((size_t)B * p.P * 3);
   w->cscore = cv.take<double>((size_t)B * p.P);
+  w->order = cv.take<int>(B);
+  w->ticket = cv.take<int>(B);
+  w->ceuler0 = cv.take<double>((size_t)B * p.P * 3);
   return cv.off;
 }
 
@@ -456,9 +461,19 @@ static matcha_status align_range(matcha_plan plan, const float *particles, const
   }
   {
     Range r("a6 Newton march");
-    if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags, nullptr,
-                                 stream)))
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->tune_newton == 2) {  // persistent CTAs on the cost-sorted queue
+      cudaError_t e = p->fp64 ? launch_newton_queue<double>(*p, (const double *)w.c, B, w.ncand,
+                                                            w.ceuler, w.cscore, w.cflags, nullptr,
+                                                            w.order, w.ticket, st)
+                              : launch_newton_queue<float>(*p, (const float *)w.c, B, w.ncand,
+                                                           w.ceuler, w.cscore, w.cflags, nullptr,
+                                                           w.order, w.ticket, st);
+      if (e != cudaSuccess) return fail_cuda(e, "newton_march");
+    } else if ((s = matcha_newton_march(plan, w.c, B, w.ncand, w.ceuler, w.cscore, w.cflags,
+                                        nullptr, stream))) {
       return s;
+    }
   }
   Range r("a7 final selection");
   return matcha_final_select(plan, B, P_per, w.ncand, w.ceuler, w.cscore, w.cflags, euler, R, score,
@@ -474,6 +489,8 @@ static AlignWs ws_at(const Plan &p, const AlignWs &w, long b0, int tstride) {
   o.c = (char *)w.c + rs * 4 * (size_t)p.nc * b0;
   o.grid = w.grid ? (char *)w.grid + rs * (size_t)p.ns * p.ns * p.ns * b0 : nullptr;
   o.cidx = w.cidx + b0 * p.P;
+  o.order = w.order + b0;
+  o.ticket = w.ticket + b0;
   o.cflags = w.cflags + b0 * p.P;
   o.ncand = w.ncand + b0;
   o.ceuler = w.ceuler + 3 * b0 * p.P;
@@ -658,8 +675,8 @@ static float time_ms(cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps,
 }
 
 matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles, const float *templates,
-                                   int B, int tstride, void *ws, size_t ws_bytes, void *stream,
-                                   matcha_tune_report *rep) {
+                                   int B, int tstride, const int *P_per, void *ws, size_t ws_bytes,
+                                   void *stream, matcha_tune_report *rep) {
   if (!plan || B < 1 || !valid_stride(tstride) || !particles || !templates || !ws || !rep)
     return MATCHA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return MATCHA_ERR_INVALID_ARG;
@@ -711,9 +728,92 @@ matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles, con
     p->tune_tc_ctas = bestC;
     rep->tc_ctas_per_sm = bestC;
   }
+  rep->soft_ms[0] = rep->soft_ms[1] = -1.0f;
+  if (err == cudaSuccess && soft_warps_ok(*p)) {  // 32-bit plans: the SOFFT kernel
+    const int Bt = tstride ? B : 1;
+    err = launch_analyze<float>(*p, particles, B, (float *)w.f, st);
+    if (err == cudaSuccess) err = launch_analyze<float>(*p, templates, Bt, (float *)w.h, st);
+    if (err == cudaSuccess)
+      err = launch_correlate<float>(*p, (const float *)w.f, (const float *)w.h, B, tstride,
+                                    (float *)w.c, st);
+    int bestK = 0;
+    float bk = -1.0f;
+    for (int k = 1; k <= 2 && err == cudaSuccess; ++k) {
+      p->tune_soft = k;
+      float t = time_ms(st, e0, e1, 3, [&]() {
+        return launch_soft<float>(*p, (const float *)w.c, B, nullptr, nullptr, w.cidx, w.ceuler,
+                                  w.cscore, w.ncand, st);
+      }, &err);
+      rep->soft_ms[k - 1] = t;
+      if (err == cudaSuccess && (bk < 0 || t < bk)) { bk = t; bestK = k; }
+    }
+    p->tune_soft = bestK;
+    rep->soft_kernel = bestK;
+  }
+  rep->newton_ms[0] = rep->newton_ms[1] = -1.0f;
+  if (err == cudaSuccess) {  // the refinement schedule, from the same start points each time
+    const int Bt = tstride ? B : 1;
+    err = p->fp64 ? launch_analyze<double>(*p, particles, B, (double *)w.f, st)
+                  : launch_analyze<float>(*p, particles, B, (float *)w.f, st);
+    if (err == cudaSuccess)
+      err = p->fp64 ? launch_analyze<double>(*p, templates, Bt, (double *)w.h, st)
+                    : launch_analyze<float>(*p, templates, Bt, (float *)w.h, st);
+    if (err == cudaSuccess)
+      err = p->fp64 ? launch_correlate<double>(*p, (const double *)w.f, (const double *)w.h, B,
+                                               tstride, (double *)w.c, st)
+                    : launch_correlate<float>(*p, (const float *)w.f, (const float *)w.h, B, tstride,
+                                              (float *)w.c, st);
+    if (err == cudaSuccess)
+      err = p->fp64 ? launch_soft<double>(*p, (const double *)w.c, B, P_per, (double *)w.grid,
+                                          w.cidx, w.ceuler, w.cscore, w.ncand, st)
+                    : launch_soft<float>(*p, (const float *)w.c, B, P_per, (float *)w.grid, w.cidx,
+                                         w.ceuler, w.cscore, w.ncand, st);
+    // the refinement overwrites its start points: each timed run starts from a copy
+    const size_t eb = sizeof(double) * 3 * (size_t)B * p->P;
+    double *start = w.ceuler0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(start, w.ceuler, eb, cudaMemcpyDeviceToDevice, st);
+    int bestN = 0;
+    float bn = -1.0f;
+    for (int k = 1; k <= 2 && err == cudaSuccess; ++k) {
+      float t = time_ms(st, e0, e1, 3, [&]() {
+        cudaError_t e2 = cudaMemcpyAsync(w.ceuler, start, eb, cudaMemcpyDeviceToDevice, st);
+        if (e2 != cudaSuccess) return e2;
+        if (k == 1)
+          return p->fp64 ? launch_newton<double>(*p, (const double *)w.c, B, w.ncand, w.ceuler,
+                                                 w.cscore, w.cflags, nullptr, st)
+                         : launch_newton<float>(*p, (const float *)w.c, B, w.ncand, w.ceuler,
+                                                w.cscore, w.cflags, nullptr, st);
+        return p->fp64 ? launch_newton_queue<double>(*p, (const double *)w.c, B, w.ncand, w.ceuler,
+                                                     w.cscore, w.cflags, nullptr, w.order, w.ticket, st)
+                       : launch_newton_queue<float>(*p, (const float *)w.c, B, w.ncand, w.ceuler,
+                                                    w.cscore, w.cflags, nullptr, w.order, w.ticket, st);
+      }, &err);
+      rep->newton_ms[k - 1] = t;
+      if (err == cudaSuccess && (bn < 0 || t < bn)) { bn = t; bestN = k; }
+    }
+    p->tune_newton = bestN;
+    rep->newton_sched = bestN;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail_cuda(err, "autotune");
+  return MATCHA_OK;
+}
+
+matcha_status matcha_plan_set_tiles(matcha_plan plan, const matcha_tune_report *ch) {
+  if (!plan || !ch) return MATCHA_ERR_INVALID_ARG;
+  Plan *p = P_(plan);
+  if (ch->analyze_shells && !analyze_shells_ok(*p, ch->analyze_shells)) return MATCHA_ERR_INVALID_ARG;
+  if (ch->tc_ctas_per_sm && (!p->tc || ch->tc_ctas_per_sm < 1 || ch->tc_ctas_per_sm > 2))
+    return MATCHA_ERR_INVALID_ARG;
+  if (ch->soft_kernel && (ch->soft_kernel < 1 || ch->soft_kernel > 2 ||
+                          (ch->soft_kernel == 2 && !soft_warps_ok(*p))))
+    return MATCHA_ERR_INVALID_ARG;
+  if (ch->newton_sched < 0 || ch->newton_sched > 2) return MATCHA_ERR_INVALID_ARG;
+  p->tune_shells = ch->analyze_shells;
+  p->tune_tc_ctas = ch->tc_ctas_per_sm;
+  p->tune_soft = ch->soft_kernel;
+  p->tune_newton = ch->newton_sched;
   return MATCHA_OK;
 }
 

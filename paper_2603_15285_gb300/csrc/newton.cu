@@ -35,6 +35,7 @@
 //   FP64 on the final level and in the plan's precision (FP32 for the 32-bit
 //   plans) on the earlier levels.
 #include <math.h>
+#include <algorithm>
 #include "internal.cuh"
 
 namespace matcha {
@@ -840,15 +841,15 @@ k_objective(const T *__restrict__ c, const T *__restrict__ rcoef, const T *__res
   for (int t = tid; t < Q * 10; t += blockDim.x) out[10 * b * Q + t] = sm.res[t];
 }
 
+// The march of all candidates of particle b by the whole CTA.
 template <typename T, bool RS>
-__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
-k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
-         const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
-         double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
-         long long *__restrict__ work) {
-  const long b = blockIdx.x;
+__device__ __forceinline__ void newton_particle(const T *__restrict__ c, const T *__restrict__ rcoef,
+                                                const T *__restrict__ seedK, const NewtonArgs &A,
+                                                const int *__restrict__ n_cand,
+                                                double *__restrict__ euler, double *__restrict__ score,
+                                                int *__restrict__ cflags, long long *__restrict__ work,
+                                                long b, unsigned char *smem_raw) {
   const int P = A.P, tid = threadIdx.x;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemLayout sm;  // staging buffers: [slots][2][stage_half(L_J)]
   int *need = carve_smem<T, RS>(smem_raw, P, A.LJ, sm);
   const int nc_b = n_cand[b];
@@ -946,6 +947,72 @@ k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
   }
 }
 
+// One CTA per particle, in index order.
+template <typename T, bool RS>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_newton(const T *__restrict__ c, const T *__restrict__ rcoef,
+         const T *__restrict__ seedK, NewtonArgs A, const int *__restrict__ n_cand,
+         double *__restrict__ euler, double *__restrict__ score, int *__restrict__ cflags,
+         long long *__restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  newton_particle<T, RS>(c, rcoef, seedK, A, n_cand, euler, score, cflags, work, blockIdx.x,
+                         smem_raw);
+}
+
+// Persistent CTAs (as many as fit on the GPU at once) pulling particles from a
+// cost-sorted queue: order[] lists the particles by decreasing refinement cost
+// (candidates to march), and a CTA takes the next entry with an atomic ticket,
+// so the most expensive particles start first and the cheap ones fill the tail
+// (longest processing time first).  Each particle's arithmetic is that of
+// k_newton, so the results are bit-identical.
+template <typename T, bool RS>
+__global__ void __launch_bounds__(NEWTON_THREADS, sizeof(T) == 8 ? 1 : 2)
+k_newton_queue(const T *__restrict__ c, const T *__restrict__ rcoef, const T *__restrict__ seedK,
+               NewtonArgs A, const int *__restrict__ n_cand, double *__restrict__ euler,
+               double *__restrict__ score, int *__restrict__ cflags, long long *__restrict__ work,
+               const int *__restrict__ order, int B, int *__restrict__ ticket) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int next;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int q = next;
+    if (q >= B) break;
+    newton_particle<T, RS>(c, rcoef, seedK, A, n_cand, euler, score, cflags, work, order[q],
+                           smem_raw);
+  }
+}
+
+// order[] = the particles by decreasing candidate count (stable in the index),
+// by a counting sort in one CTA; also resets the queue's ticket.
+__global__ void k_cost_order(const int *__restrict__ n_cand, int B, int P, int *__restrict__ order,
+                             int *__restrict__ ticket) {
+  __shared__ int start[MATCHA_MAX_P + 2];
+  const int tid = threadIdx.x;
+  if (tid <= P + 1) start[tid] = 0;
+  __syncthreads();
+  for (int b = tid; b < B; b += blockDim.x) atomicAdd(&start[P - min(max(n_cand[b], 0), P) + 1], 1);
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 1; k <= P + 1; ++k) start[k] += start[k - 1];
+    *ticket = 0;
+  }
+  __syncthreads();
+  // stable placement: each bin is filled in index order by one warp per bin
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k <= P; k += nw) {
+    int pos = start[k];
+    for (int b0 = 0; b0 < B; b0 += 32) {
+      const int b = b0 + lane;
+      const bool in = b < B && P - min(max(n_cand[b], 0), P) == k;
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) order[pos + __popc(m & ((1u << lane) - 1u))] = b;
+      pos += __popc(m);
+    }
+  }
+}
+
 // Lanes per warp sub-slot: one per candidate, at least 16.
 static int newton_cpw(int P) { return P <= 16 ? 16 : 32; }
 
@@ -1007,6 +1074,43 @@ cudaError_t launch_newton(const Plan &p, const T *c, int B, const int *n_cand, d
                                                       A, n_cand, euler, score, cflags, work);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_newton_queue(const Plan &p, const T *c, int B, const int *n_cand, double *euler,
+                                double *score, int *cflags, long long *work, int *order,
+                                int *ticket, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  NewtonArgs A;
+  A.LJ = p.LJ; A.nlev = p.nlev; A.M = p.M; A.P = p.P;
+  A.cpw = newton_cpw(p.P);
+  A.nslots = newton_slots(p, sizeof(T));
+  if (A.nslots == 0) return cudaErrorInvalidConfiguration;
+  for (int i = 0; i < MATCHA_MAX_LEVELS; ++i) A.Ls[i] = i < p.nlev ? p.Ls[i] : 0;
+  A.tol = p.step_tol; A.acc_tol = p.accept_tol; A.grad = p.refine; A.nc = p.nc;
+  const size_t smem = newton_smem_bytes(p, sizeof(T), A.nslots);
+  k_cost_order<<<1, 1024, 0, st>>>(n_cand, B, p.P, order, ticket);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NEWTON_THREADS, smem);
+    const int grid = std::max(1, std::min(B, std::max(per_sm, 1) * sms));
+    kern<<<grid, NEWTON_THREADS, smem, st>>>(c, (const T *)p.rcoef, (const T *)p.seedK, A, n_cand,
+                                             euler, score, cflags, work, order, B, ticket);
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (newton_rescaled(p, sizeof(T))) { go(k_newton_queue<T, true>); return cudaGetLastError(); }
+  }
+  go(k_newton_queue<T, false>);
+  return cudaGetLastError();
+}
+template cudaError_t launch_newton_queue<float>(const Plan &, const float *, int, const int *,
+                                                double *, double *, int *, long long *, int *,
+                                                int *, cudaStream_t);
+template cudaError_t launch_newton_queue<double>(const Plan &, const double *, int, const int *,
+                                                 double *, double *, int *, long long *, int *,
+                                                 int *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_objective(const Plan &p, const T *c, int B, int L, int Q, const double *pts,

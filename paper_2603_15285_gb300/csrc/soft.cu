@@ -947,6 +947,253 @@ k_soft_chunk(const T *__restrict__ c, long nc, int L0, int ns, const int *__rest
 
 constexpr int SOFT_KB = 4;
 
+// Warp-per-slice variant (32-bit plans, grids of a few tens of points per
+// angle): one CTA per particle; in each pass warp w computes beta slice
+// p NW + w on its own (beta transform, the two DFT stages, its slice of the
+// grid into a ring of NW + 2 slices), separated only by warp barriers; one
+// CTA barrier per pass, then the exact 26-neighbour test of every slice whose
+// neighbours are ready (early exit on the first neighbour that precedes the
+// point), the survivors merged by warp 0 into the sorted best-P list.  The
+// per-point arithmetic and its order are those of k_soft_chunk, so the grid,
+// the candidates and their order are bit-identical to it.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 2)
+k_soft_warps(const float *__restrict__ c, long nc, int L0, int ns, const int *__restrict__ pair_base,
+             const float *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+             const float *__restrict__ tw, int P_max, const int *__restrict__ P_per,
+             float *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
+             double *__restrict__ score_out, int *__restrict__ n_cand_out) {
+  using T = float;
+  constexpr int NR = NW + 2;
+  const long b = blockIdx.x;
+  const int W = 2 * L0 + 1, np0 = (L0 + 1) * (L0 + 1), n2 = ns * ns;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int capc = (NW + 1) * ((ns + 1) / 2) * ((ns + 1) / 2);  // maxima of one pass's slices
+  const int nsp = (ns + 3) / 4 * 4, nq4 = nsp / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto al4 = [](long x) { return (x + 3) & ~3L; };
+  T *ring = reinterpret_cast<T *>(smem_raw);           // [NR][n2]
+  const long per_w = al4(2 * W * W) + al4(2 * (L0 + 1) * nsp);
+  T *wbuf = ring + al4(NR * n2);                        // [NW][Sg | G]
+  T *Eg = wbuf + NW * per_w;                            // [W][nsp] complex
+  T *Aa = Eg + al4(2 * W * nsp);                        // [2(L0+1)][nsp]
+  T *cst = Aa + al4(2 * (L0 + 1) * nsp);                // [nc0][4]
+  T *cv = cst + 4 * nc0;                                // [capc]
+  T *rv = cv + capc;                                    // [32]
+  int *ci = reinterpret_cast<int *>(rv + 32);           // [capc]
+  int *ri = ci + capc;                                  // [32]
+  int *counters = ri + 32;                              // [0] pass count, [1] kept
+  const FastDiv dns(ns), dq4(nq4);
+  for (int t = tid; t < W * nsp; t += NT) {
+    int n = t / nsp, j = t - n * nsp;
+    T er = 0, ei = 0;
+    if (j < ns) {
+      int tt = ((n - L0) * j) % ns;
+      if (tt < 0) tt += ns;
+      er = tw[2 * tt]; ei = tw[2 * tt + 1];
+    }
+    Eg[2 * t] = er; Eg[2 * t + 1] = ei;
+  }
+  for (int t = tid; t < 2 * (L0 + 1) * nsp; t += NT) {
+    int cc = t / nsp, i = t - cc * nsp, m = cc >> 1;
+    T v = 0;
+    if (i < ns) {
+      int tt = (m * i) % ns;
+      T w = m == 0 ? T(1) : T(2);
+      v = (cc & 1) ? -w * tw[2 * tt + 1] : w * tw[2 * tt];
+    }
+    Aa[t] = v;
+  }
+  {
+    const T *cg = c + 4 * b * nc;
+    const FastDiv dl(L0 + 1);
+    for (int t = tid; t < np0 * (L0 + 1); t += NT) {
+      int q = dl.div(t), e = t - q * (L0 + 1);
+      int m = isqrt_floor(q);
+      if (e <= L0 - m) {
+        const T *src = cg + pair_base[q] + 8L * e;
+        T *dst = cst + 4L * (pair_off0[q] + e);
+        dst[0] = src[0]; dst[1] = src[2]; dst[2] = src[4]; dst[3] = src[6];
+      }
+    }
+  }
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  if (tid < 32) { rv[tid] = 0; ri[tid] = INT_MAX; }
+  if (tid == 0) counters[1] = 0;
+  __syncthreads();
+  T *Sg = wbuf + warp * per_w;
+  T *G = Sg + al4(2 * W * W);
+  int tested = 0;  // slices [0, tested) tested
+  for (int k0 = 0; k0 < ns; k0 += NW) {
+    const int k = k0 + warp;
+    if (k < ns) {
+      // beta transform of slice k
+      for (int q = lane; q < np0; q += 32) {
+        int m = isqrt_floor(q), n = q - m * m - m;
+        const T *cp = cst + 4L * pair_off0[q];
+        const T *dp = soft_d + (long)k * nc0 + pair_off0[q];
+        T ar = 0, ai = 0, br = 0, bi = 0;
+        for (int l = m; l <= L0; ++l) {
+          T d = dp[l - m];
+          const T *e = cp + 4 * (l - m);
+          ar = fma(e[0], d, ar); ai = fma(e[1], d, ai);
+          br = fma(e[2], d, br); bi = fma(e[3], d, bi);
+        }
+        if ((m - n) & 1) { br = -br; bi = -bi; }
+        int i0 = (m + L0) * W + (n + L0);
+        Sg[2 * i0] = ar; Sg[2 * i0 + 1] = ai;
+        if (q != 0) { int i1 = (-m + L0) * W + (-n + L0); Sg[2 * i1] = ar; Sg[2 * i1 + 1] = -ai; }
+        if (n != m && n != -m) {
+          int i2 = (n + L0) * W + (m + L0), i3 = (-n + L0) * W + (-m + L0);
+          Sg[2 * i2] = br; Sg[2 * i2 + 1] = bi;
+          Sg[2 * i3] = br; Sg[2 * i3 + 1] = -bi;
+        }
+      }
+      __syncwarp();
+      // G_m(j) = sum_n S_mn e^{i n g_j}; items of one m and 4 j
+      for (int t = lane; t < (L0 + 1) * nq4; t += 32) {
+        int m = dq4.div(t), j0 = (t - m * nq4) * 4;
+        const T *row = Sg + 2 * (m + L0) * W;
+        T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+        for (int n = 0; n < W; ++n) {
+          T sr = row[2 * n], si = row[2 * n + 1];
+          const T *e = Eg + 2 * (n * nsp + j0);
+          float4 e01 = *reinterpret_cast<const float4 *>(e), e23 = *reinterpret_cast<const float4 *>(e + 4);
+          T er[4] = {e01.x, e01.z, e23.x, e23.z}, ei[4] = {e01.y, e01.w, e23.y, e23.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            re[u] = fma(sr, er[u], fma(-si, ei[u], re[u]));
+            im[u] = fma(sr, ei[u], fma(si, er[u], im[u]));
+          }
+        }
+        T *Gm = G + 2 * m * nsp;  // [m][re|im][j]
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { Gm[j0 + u] = re[u]; Gm[nsp + j0 + u] = im[u]; }
+      }
+      __syncwarp();
+      // C(i, k, j) = sum_c A[c][i] B[c][j]; 4 x 4 tiles
+      T *dst = ring + (k % NR) * n2;
+      for (int t = lane; t < nq4 * nq4; t += 32) {
+        int iq = dq4.div(t), i0 = iq * 4, j0 = (t - iq * nq4) * 4;
+        T o[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) o[u][v] = 0;
+        for (int cc = 0; cc < 2 * (L0 + 1); ++cc) {
+          float4 av = *reinterpret_cast<const float4 *>(Aa + cc * nsp + i0);
+          float4 bv = *reinterpret_cast<const float4 *>(G + cc * nsp + j0);
+          T a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u][v] = fma(a4[u], b4[v], o[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (i0 + u < ns && j0 + v < ns) dst[(i0 + u) * ns + j0 + v] = o[u][v];
+      }
+      if (grid_out) {
+        __syncwarp();
+        T *go = grid_out + b * (long)ns * n2;
+        for (int r = lane; r < n2; r += 32) {
+          int i = dns.div(r), j = r - i * ns;
+          go[((long)i * ns + k) * ns + j] = dst[r];
+        }
+      }
+    }
+    if (tid == 0) counters[0] = 0;
+    __syncthreads();
+    // slices whose beta neighbours are ready
+    const int done = min(ns, k0 + NW);
+    const int t1 = done == ns ? ns : done - 1;
+    const int nt_ = t1 - tested;
+    for (int t = tid; t < nt_ * n2; t += NT) {
+      const int kk = t / n2, r = t - kk * n2, kq0 = tested + kk;
+      const int i = dns.div(r), j = r - i * ns;
+      const T v = ring[(kq0 % NR) * n2 + r];
+      if (!(v == v)) continue;
+      const int p = (i * ns + kq0) * ns + j;
+      bool ok = true;
+      for (int dk = -1; dk <= 1 && ok; ++dk) {
+        int kq = kq0 + dk;
+        if (kq < 0 || kq >= ns) continue;
+        const T *sl = ring + (kq % NR) * n2;
+        for (int di = -1; di <= 1 && ok; ++di) {
+          int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+          for (int dj = -1; dj <= 1; ++dj) {
+            if (!di && !dk && !dj) continue;
+            int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+            int q = (ii * ns + kq) * ns + jj;
+            if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+          }
+        }
+      }
+      if (ok) {
+        int pos = atomicAdd(&counters[0], 1);
+        if (pos < capc) { cv[pos] = v; ci[pos] = p; }
+      }
+    }
+    tested = t1;
+    __syncthreads();
+    if (tid < 32) {  // warp 0: insert into the sorted best-P list, in (value, index) order
+      T myv = rv[lane];
+      int myi = ri[lane];
+      int kept = counters[1];
+      const int cnt = min(counters[0], capc);
+      for (int e = 0; e < cnt; ++e) {
+        T v = cv[e];
+        int i = ci[e];
+        bool before = lane < kept && precedes(myv, myi, v, i);
+        int pos = __popc(__ballot_sync(0xffffffffu, before));
+        T upv = __shfl_up_sync(0xffffffffu, myv, 1);
+        int upi = __shfl_up_sync(0xffffffffu, myi, 1);
+        if (pos < Pb) {
+          if (lane > pos) { myv = upv; myi = upi; }
+          if (lane == pos) { myv = v; myi = i; }
+          kept = min(kept + 1, Pb);
+        }
+      }
+      rv[lane] = myv;
+      ri[lane] = myi;
+      if (lane == 0) counters[1] = kept;
+    }
+    __syncthreads();
+  }
+  const int kept = counters[1];
+  for (int r = tid; r < P_max; r += NT) {
+    long o = b * P_max + r;
+    if (r < kept) {
+      int i = ri[r];
+      idx_out[o] = i;
+      score_out[o] = (double)rv[r];
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    } else {
+      idx_out[o] = -1;
+      score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+      euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+    }
+  }
+  if (tid == 0) n_cand_out[b] = kept;
+}
+
+template <int NW>
+size_t soft_warps_smem(const Plan &p) {
+  auto al4 = [](size_t x) { return (x + 3) & ~size_t(3); };
+  const size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns, nsp = (p.ns + 3) / 4 * 4;
+  const size_t capc = (size_t)(NW + 1) * ((p.ns + 1) / 2) * ((p.ns + 1) / 2);
+  const size_t per_w = al4(2 * W * W) + al4(2 * (p.L0 + 1) * nsp);
+  return 4 * (al4((NW + 2) * n2) + NW * per_w + al4(2 * W * nsp) + al4(2 * (p.L0 + 1) * nsp) +
+              4 * (size_t)p.nc0 + capc + 32) +
+         4 * (capc + 32 + 4) + 16;
+}
+
 size_t soft_chunk_smem(const Plan &p, size_t ts) {
   size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns;
   size_t capc = (size_t)SOFT_KB * ((p.ns + 1) / 2) * ((p.ns + 1) / 2);
@@ -966,9 +1213,11 @@ size_t soft_stream_smem(const Plan &p, size_t ts) {
 
 // True when one of the fused kernels (chunked, streaming or FP32 fused) serves
 // the plan, so the full grid need not be materialised.
+bool soft_warps_ok(const Plan &p);
+
 bool soft_grid_optional(const Plan &p) {
   const size_t ts = p.fp64 ? 8 : 4;
-  return soft_chunk_smem(p, ts) <= 227 * 1024 - 1024 || soft_stream_smem(p, ts) <= 227 * 1024 - 1024 ||
+  return soft_warps_ok(p) || soft_chunk_smem(p, ts) <= 227 * 1024 - 1024 || soft_stream_smem(p, ts) <= 227 * 1024 - 1024 ||
          (!p.fp64 && soft_fused_ok(p));
 }
 
@@ -980,10 +1229,27 @@ bool soft_fits(const Plan &p) {
   return ts * (2 * W * W + 2 * (size_t)(p.L0 + 1) * p.ns) <= 227 * 1024 - 1024;
 }
 
+constexpr int SOFT_NW = 6;  // slices per pass of k_soft_warps (two CTAs per SM at L0 = 8, K = 2)
+
+bool soft_warps_ok(const Plan &p) {
+  return !p.fp64 && soft_warps_smem<SOFT_NW>(p) <= 113 * 1024;
+}
+
 template <typename T>
 cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *grid, int *idx,
                         double *euler, double *score, int *n_cand, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
+  // the warp-per-slice kernel only when chosen (autotuner or matcha_plan_set_tiles):
+  // measured slower than the chunked kernel at L0 = 8, K = 2 (0.43 against 0.16 ms
+  // for 256 particles)
+  if (sizeof(T) == 4 && p.tune_soft == 2 && soft_warps_ok(p)) {
+    size_t smem = soft_warps_smem<SOFT_NW>(p);
+    cudaFuncSetAttribute(k_soft_warps<SOFT_NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_soft_warps<SOFT_NW><<<B, SOFT_NW * 32, smem, st>>>(
+        (const float *)c, p.nc, p.L0, p.ns, p.pair_base, (const float *)p.soft_d, p.pair_off0,
+        p.nc0, (const float *)p.soft_tw, p.P, P_per, (float *)grid, idx, euler, score, n_cand);
+    return cudaGetLastError();
+  }
   {
     size_t smem = soft_chunk_smem(p, sizeof(T));
     if (smem <= 227 * 1024 - 1024) {

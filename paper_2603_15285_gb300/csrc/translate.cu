@@ -516,8 +516,10 @@ cudaError_t launch_shift_search(const Plan &p, const float *f, const float *u, i
   fd.npass = p.fft_npass;
   for (int q = 0; q < 16; ++q) fd.radix[q] = p.fft_radix[q];
   const size_t cs = sizeof(C2<T>);
-  const int NB0 = N >= 128 ? 4 : 2048 / N > 16 ? 16 : 2048 / N;
-  const int NB = 16;
+  // lines per CTA: about 4096 elements (a whole 64 x 64 plane), at least 16
+  // columns for the strided passes so their rows stay coalesced
+  const int NB0 = N * N <= 4096 ? N : (4096 / N > 0 ? 4096 / N : 1);
+  const int NB = N <= 64 ? N : (4096 / N > 16 ? 4096 / N : 16);
   size_t sm0 = cs * 2 * (size_t)NB0 * (N + 1), sm1 = cs * 2 * (size_t)NB * (N + 1);
   size_t smax = sm0 > sm1 ? sm0 : sm1;
   cudaFuncSetAttribute(k_fft_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);

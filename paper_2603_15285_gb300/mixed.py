@@ -70,7 +70,8 @@ class MixedBatch:
                             score=torch.empty((B,), dtype=torch.float64, device=dev),
                             best_p=torch.empty((B,), dtype=torch.int32, device=dev),
                             flags=torch.empty((B,), dtype=torch.int32, device=dev))
-            self.tune.append(plan.autotune(parts, g["templates"], ws=d["ws"]) if autotune else None)
+            self.tune.append(plan.autotune(parts, g["templates"], ws=d["ws"], P_per=g.get("P_per"))
+                             if autotune else None)
             self.groups.append(d)
         self.graph = None
 

@@ -88,7 +88,7 @@ def test_newer_entry_points_check_arguments_on_the_host(L):
     assert L.matcha_template_grad_workspace_size(None, 4, 0, ctypes.byref(sz)) == 1
     assert L.matcha_template_grad(None, None, None, 4, 0, None, None, None, None, None, None,
                                   None, 0, None) == 1
-    assert L.matcha_plan_autotune(None, None, None, 4, 1, None, 0, None, None) == 1
+    assert L.matcha_plan_autotune(None, None, None, 4, 1, None, None, 0, None, None) == 1
     assert L.matcha_plan_device_status(None, ctypes.byref(bits)) == 1
     assert L.matcha_plan_set_wait_limit(None, 0) == 1
     assert L.matcha_host_workspace_size(None, 4, 1, ctypes.byref(sz)) == 1
