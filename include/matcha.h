@@ -287,7 +287,8 @@ matcha_status matcha_align_host(matcha_plan plan, const float *particles, const 
  * analysis CTA (1, 2, 4 or 8, those whose shared memory fits), for TF32 /
  * BF16 plans the tensor-core contraction's CTAs per SM (1 or 2), and for
  * 32-bit plans whose grid fits it the SOFFT search kernel (1: the chunked
- * kernels, 2: one warp per beta slice), and the refinement schedule of
+ * kernels, 2: one warp per beta slice, 3: the register-tiled chunked kernel,
+ * the built-in choice where it applies), and the refinement schedule of
  * matcha_align (1: one CTA per particle, 2: persistent CTAs on a cost-sorted
  * queue, longest processing time first).  P_per_dev (nullable) gives the
  * per-particle candidate counts as for matcha_align.  Uses the matcha_align workspace for
@@ -300,7 +301,7 @@ typedef struct {
   int tc_ctas_per_sm;      /* 0 when the plan's contraction runs on the CUDA cores */
   float tc_ms[2];          /* candidates 1, 2 CTAs per SM */
   int soft_kernel;         /* 0 when only one SOFFT kernel serves the plan */
-  float soft_ms[2];        /* candidates 1 (chunked), 2 (warp per slice) */
+  float soft_ms[3];        /* candidates 1 (chunked), 2 (warp per slice), 3 (register-tiled) */
   int newton_sched;        /* matcha_align's refinement: 1 a CTA per particle in index
                               order, 2 persistent CTAs pulling particles from a queue
                               sorted by decreasing candidate count */

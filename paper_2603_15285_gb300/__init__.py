@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
 class TuneReport(ctypes.Structure):
     _fields_ = [("analyze_shells", ctypes.c_int), ("analyze_ms", ctypes.c_float * 4),
                 ("tc_ctas_per_sm", ctypes.c_int), ("tc_ms", ctypes.c_float * 2),
-                ("soft_kernel", ctypes.c_int), ("soft_ms", ctypes.c_float * 2),
+                ("soft_kernel", ctypes.c_int), ("soft_ms", ctypes.c_float * 3),
                 ("newton_sched", ctypes.c_int), ("newton_ms", ctypes.c_float * 2)]
 
 

@@ -132,6 +132,18 @@ template <typename T>
 __device__ __forceinline__ typename Vec4<T>::type ld4(const T *p) {
   return *reinterpret_cast<const typename Vec4<T>::type *>(p);
 }
+// (re, im) and (cos, sin) pairs move as one 8- or 16-byte shared access
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type ld2(const T *p) {
+  return *reinterpret_cast<const typename Vec2<T>::type *>(p);
+}
+template <typename T>
+__device__ __forceinline__ void st2(T *p, typename Vec2<T>::type v) {
+  *reinterpret_cast<typename Vec2<T>::type *>(p) = v;
+}
 
 template <typename T, int G>
 __global__ void __launch_bounds__(256)
@@ -218,8 +230,9 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
       int r = dhalf.div(t), kk = t - r * half;
       int ka = kk, kb = kk ? np - kk : half;
       T rho = RH[r], pz = RZ[r];
-      va[u] = sample(c0 + rho * PH[2 * ka], c0 + rho * PH[2 * ka + 1], pz);
-      vb[u] = sample(c0 + rho * PH[2 * kb], c0 + rho * PH[2 * kb + 1], pz);
+      const typename Vec2<T>::type pa = ld2(PH + 2 * ka), pb = ld2(PH + 2 * kb);
+      va[u] = sample(c0 + rho * pa.x, c0 + rho * pa.y, pz);
+      vb[u] = sample(c0 + rho * pb.x, c0 + rho * pb.y, pz);
       rr[u] = r; kr[u] = kk;
     }
 #pragma unroll
@@ -282,9 +295,10 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
         for (int v = 0; v < 4; ++v) {
           int m = 2 * (c0 + v) + par;
           if (m <= L) {
-            T *o = F + 2 * ((r0 + u) * Mp + m);
-            o[0] = re[u][v] + e0 + (par ? -eh : eh);
-            o[1] = im[u][v];
+            typename Vec2<T>::type o;
+            o.x = re[u][v] + e0 + (par ? -eh : eh);
+            o.y = im[u][v];
+            st2(F + 2 * ((r0 + u) * Mp + m), o);
           }
         }
       }
@@ -300,9 +314,12 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   for (int t = tid; t < Gs * (nt / 2) * (L + 1); t += NT) {
     int gj = dL1.div(t), m = t - gj * (L + 1), g = dnh.div(gj), j = gj - g * (nt / 2);
     T *fa = F + 2 * ((g * nt + j) * Mp + m), *fb = F + 2 * ((g * nt + nt - 1 - j) * Mp + m);
-    T ar = fa[0], ai = fa[1], br = fb[0], bi = fb[1];
-    fa[0] = ar + br; fa[1] = ai + bi;
-    fb[0] = ar - br; fb[1] = ai - bi;
+    const typename Vec2<T>::type a = ld2(fa), bq = ld2(fb);
+    typename Vec2<T>::type sa, sb;
+    sa.x = a.x + bq.x; sa.y = a.y + bq.y;
+    sb.x = a.x - bq.x; sb.y = a.y - bq.y;
+    st2(fa, sa);
+    st2(fb, sb);
   }
   __syncthreads();
   for (int lm = tid; lm < nlm; lm += NT) {
@@ -319,9 +336,9 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
       const T *fj = F + 2 * ((odd ? nt - 1 - j : j) * Mp + m);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const T *f = fj + 2 * g * nt * Mp;
-        ar[g] = fma(w, f[0], ar[g]);
-        ai[g] = fma(w, f[1], ai[g]);
+        const typename Vec2<T>::type f = ld2(fj + 2 * g * nt * Mp);
+        ar[g] = fma(w, f.x, ar[g]);
+        ai[g] = fma(w, f.y, ai[g]);
       }
     }
 #pragma unroll

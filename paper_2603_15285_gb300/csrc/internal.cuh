@@ -24,7 +24,8 @@ struct Plan {
   // them changes any result bit
   int tune_shells = 0;   // shells per analysis CTA (1, 2, 4, 8)
   int tune_tc_ctas = 0;  // tensor-core contraction CTAs per SM (1, 2)
-  int tune_soft = 0;     // SOFFT search kernel: 1 the chunked kernels, 2 warp per slice
+  int tune_soft = 0;     // SOFFT search kernel: 1 the chunked kernels, 2 warp per slice,
+                         // 3 register-tiled
   int tune_newton = 0;   // refinement schedule: 1 a CTA per particle, 2 persistent cost-sorted queue
   long wait_limit = -1;  // mbarrier polls before a wait gives up (-1: the built-in limit)
   int nt, np, nlm, npairs, npairs0, ns;
@@ -136,6 +137,7 @@ bool analyze_shells_ok(const Plan &p, int G);  // G shells per analysis CTA fit
 bool soft_grid_optional(const Plan &p);  // the SOFFT search can skip writing the grid
 bool soft_fits(const Plan &p);           // some SOFFT kernel serves the plan
 bool soft_warps_ok(const Plan &p);       // the warp-per-slice SOFFT kernel serves the plan
+bool soft_tile_ok(const Plan &p);        // the register-tiled SOFFT kernel serves the plan
 // Translation search (translate.cu): volume poses, the box FFT, the cross
 // spectrum and the windowed inverse DFT of the correlation.
 cudaError_t launch_pose_volumes(int N, const float *vol, int B, long vol_stride, const double *R,

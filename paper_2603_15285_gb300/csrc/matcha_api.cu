@@ -728,8 +728,8 @@ matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles, con
     p->tune_tc_ctas = bestC;
     rep->tc_ctas_per_sm = bestC;
   }
-  rep->soft_ms[0] = rep->soft_ms[1] = -1.0f;
-  if (err == cudaSuccess && soft_warps_ok(*p)) {  // 32-bit plans: the SOFFT kernel
+  rep->soft_ms[0] = rep->soft_ms[1] = rep->soft_ms[2] = -1.0f;
+  if (err == cudaSuccess && (soft_warps_ok(*p) || soft_tile_ok(*p))) {  // 32-bit plans: the SOFFT kernel
     const int Bt = tstride ? B : 1;
     err = launch_analyze<float>(*p, particles, B, (float *)w.f, st);
     if (err == cudaSuccess) err = launch_analyze<float>(*p, templates, Bt, (float *)w.h, st);
@@ -738,7 +738,8 @@ matcha_status matcha_plan_autotune(matcha_plan plan, const float *particles, con
                                     (float *)w.c, st);
     int bestK = 0;
     float bk = -1.0f;
-    for (int k = 1; k <= 2 && err == cudaSuccess; ++k) {
+    for (int k = 1; k <= 3 && err == cudaSuccess; ++k) {
+      if ((k == 2 && !soft_warps_ok(*p)) || (k == 3 && !soft_tile_ok(*p))) continue;
       p->tune_soft = k;
       float t = time_ms(st, e0, e1, 3, [&]() {
         return launch_soft<float>(*p, (const float *)w.c, B, nullptr, nullptr, w.cidx, w.ceuler,
@@ -806,8 +807,9 @@ matcha_status matcha_plan_set_tiles(matcha_plan plan, const matcha_tune_report *
   if (ch->analyze_shells && !analyze_shells_ok(*p, ch->analyze_shells)) return MATCHA_ERR_INVALID_ARG;
   if (ch->tc_ctas_per_sm && (!p->tc || ch->tc_ctas_per_sm < 1 || ch->tc_ctas_per_sm > 2))
     return MATCHA_ERR_INVALID_ARG;
-  if (ch->soft_kernel && (ch->soft_kernel < 1 || ch->soft_kernel > 2 ||
-                          (ch->soft_kernel == 2 && !soft_warps_ok(*p))))
+  if (ch->soft_kernel && (ch->soft_kernel < 1 || ch->soft_kernel > 3 ||
+                          (ch->soft_kernel == 2 && !soft_warps_ok(*p)) ||
+                          (ch->soft_kernel == 3 && !soft_tile_ok(*p))))
     return MATCHA_ERR_INVALID_ARG;
   if (ch->newton_sched < 0 || ch->newton_sched > 2) return MATCHA_ERR_INVALID_ARG;
   p->tune_shells = ch->analyze_shells;

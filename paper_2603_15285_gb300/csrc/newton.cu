@@ -148,20 +148,23 @@ template <typename T> __device__ __forceinline__ v2<T> vld(unsigned a0, unsigned
   return vset<T>(x, y);
 }
 
-// Offset, in (group, l) entries of the bandwidth-LJ layout, of group (m, j):
-// sum_{m'<m} (m'+1)(LJ-m'+1) + j (LJ-m+1), the sum in closed form.
-__device__ __forceinline__ int group_offset(int m, int j, int LJ) {
-  const int t = m * (m + 1) / 2;
-  return (LJ + 2) * t - t * (2 * m + 1) / 3 + j * (LJ - m + 1);
-}
-
 struct Group {
   int m, na, off;  // order, first partner's n, offset in (group, l) entries
 };
-__device__ __forceinline__ Group group_of(int g, int LJ) {
-  const int m = tri_floor(g), j = g - m * (m + 1) / 2;
-  return {m, 2 * j - m, group_offset(m, j, LJ)};
-}
+// The groups of a sub-slot come in increasing g: the order m and the offset
+// of the first group of m advance with g instead of being solved for.
+struct GroupWalk {
+  int m = 0, tri = 0, base = 0;  // tri = m(m+1)/2, base = offset of group (m, 0)
+  __device__ __forceinline__ Group at(int g, int LJ) {
+    while (g >= tri + m + 1) {
+      base += (m + 1) * (LJ - m + 1);
+      tri += m + 1;
+      ++m;
+    }
+    const int j = g - tri;
+    return {m, 2 * j - m, base + j * (LJ - m + 1)};
+  }
+};
 
 // Staging buffer of one sub-slot, per half (double buffering), in reals:
 // [4] seed norms (K_a, K_b, 0, 0), then per degree entry 16 reals: the 8 c
@@ -501,43 +504,68 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   T *ph = (T *)sm.ea;    // [4][RW][PS]: cos k a, sin k a, cos k g, sin k g
   T *pw = (T *)sm.pw;    // [2][NPW][PS]: PW_PAD zeros, then ch^k (sh^k), k = 0..2LJ+3
   const int tid = threadIdx.x;
-  if (tid < P && need[tid]) {
-    T al = (T)pts[3 * tid], be = (T)pts[3 * tid + 1], ga = (T)pts[3 * tid + 2];
-    T *e = evp + 8 * tid;
-    e[0] = tcos(be); e[1] = tsin(be);
-    e[2] = tcos(be * T(0.5)); e[3] = tsin(be * T(0.5));
-    e[4] = tcos(al); e[5] = tsin(al);
-    e[6] = tcos(ga); e[7] = tsin(ga);
-  }
-  __syncthreads();
-  const int npk = 2 * L + 4;  // powers k = 0..2L+3
-  const FastDiv dw(npk);
-  for (int t = tid; t < 2 * P * npk; t += blockDim.x) {
-    int pr = dw.div(t), k = t - pr * npk;
-    int p = pr >> 1, which = pr & 1;
-    if (!need[p]) continue;
-    if (RS) {  // mantissa rows, then exponent rows (2 NPW rows further on)
-      float mt;
-      int ex;
-      xpow((float)evp[8 * p + 2 + which], k, mt, ex);
-      pw[(which * NPW + PW_PAD + k) * PS + p] = (T)mt;
-      pw[((2 + which) * NPW + PW_PAD + k) * PS + p] = (T)ex;
-    } else {
-      pw[(which * NPW + PW_PAD + k) * PS + p] = ipow_t(evp[8 * p + 2 + which], k);
+  // per candidate: (cos, sin) of beta, beta/2, alpha, gamma, one angle per thread
+  for (int t = tid; t < 4 * P; t += blockDim.x) {
+    const int p = t >> 2, a = t & 3;
+    if (need[p]) {
+      const double *q = pts + 3 * p;
+      const T x = a == 0 ? (T)q[1] : a == 1 ? (T)q[1] * T(0.5) : (T)q[a == 2 ? 0 : 2];
+      evp[8 * p + 2 * a] = tcos(x);
+      evp[8 * p + 2 * a + 1] = tsin(x);
     }
   }
-  if (tid < 2 * P) {
-    int p = tid >> 1, which = tid & 1;
+  __syncthreads();
+  // powers k = 0..2L+3 of cos(beta/2) and sin(beta/2): runs of 8 consecutive
+  // powers per item, the first by binary powering, the rest by one product each
+  constexpr int RUN = 8;
+  const int npk = 2 * L + 4, nrun = (npk + RUN - 1) / RUN;
+  const FastDiv dw(nrun);
+  for (int t = tid; t < 2 * P * nrun; t += blockDim.x) {
+    int pr = dw.div(t), k0 = (t - pr * nrun) * RUN;
+    int p = pr >> 1, which = pr & 1;
+    if (!need[p]) continue;
+    const T x = evp[8 * p + 2 + which];
+    const int k1 = min(k0 + RUN, npk);
+    if (RS) {  // mantissa rows, then exponent rows (2 NPW rows further on)
+      for (int k = k0; k < k1; ++k) {
+        float mt;
+        int ex;
+        xpow((float)x, k, mt, ex);
+        pw[(which * NPW + PW_PAD + k) * PS + p] = (T)mt;
+        pw[((2 + which) * NPW + PW_PAD + k) * PS + p] = (T)ex;
+      }
+    } else {
+      T v = ipow_t(x, k0);
+      T *o = pw + (which * NPW + PW_PAD + k0) * PS + p;
+      o[0] = v;
+      for (int k = k0 + 1; k < k1; ++k) {
+        v *= x;
+        o += PS;
+        o[0] = v;
+      }
+    }
+  }
+  // phase rows cos, sin of k alpha and k gamma, k = -L..L+1: eight chains per
+  // (candidate, angle), chain q holding k = q, q + 8, ... (start e^{i q x},
+  // step e^{8 i x})
+  for (int t = tid; t < 16 * P; t += blockDim.x) {
+    const int pq = t >> 3, q = t & 7, p = pq >> 1, which = pq & 1;
     if (need[p]) {
-      T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
+      const T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
       T *cr_ = ph + ((2 * which) * RW + LJ) * PS + p, *ci_ = cr_ + RW * PS;
+      // e^{2ix}, e^{4ix}, e^{8ix} and e^{iqx} by binary powering
+      const T c2 = c1 * c1 - s1 * s1, s2 = T(2) * c1 * s1;
+      const T c4 = c2 * c2 - s2 * s2, s4 = T(2) * c2 * s2;
+      const T c8 = c4 * c4 - s4 * s4, s8 = T(2) * c4 * s4;
       T cr = 1, ci = 0;
-      cr_[0] = 1; ci_[0] = 0;
-      for (int m = 1; m <= L + 1; ++m) {
-        T nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
-        cr = nr; ci = ni;
+      if (q & 1) { cr = c1; ci = s1; }
+      if (q & 2) { const T nr = cr * c2 - ci * s2, ni = cr * s2 + ci * c2; cr = nr; ci = ni; }
+      if (q & 4) { const T nr = cr * c4 - ci * s4, ni = cr * s4 + ci * c4; cr = nr; ci = ni; }
+      for (int m = q; m <= L + 1; m += 8) {
         cr_[m * PS] = cr; ci_[m * PS] = ci;
-        if (m <= L) { cr_[-m * PS] = cr; ci_[-m * PS] = -ci; }
+        if (m > 0 && m <= L) { cr_[-m * PS] = cr; ci_[-m * PS] = -ci; }
+        const T nr = cr * c8 - ci * s8, ni = cr * s8 + ci * c8;
+        cr = nr; ci = ni;
       }
     }
   }
@@ -592,14 +620,15 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   if (slot < nslots && slot < ng) {
     int cur = 0, k = 0;
     int g = group_at(0);
-    Group gc = group_of(g, LJ);
+    GroupWalk walk;
+    Group gc = walk.at(g, LJ);
     issue(gc, g, stg);
     cp_async_commit();
     while (g < ng) {
       const int gn = group_at(k + 1);
       Group gnx = gc;
       if (gn < ng) {
-        gnx = group_of(gn, LJ);
+        gnx = walk.at(gn, LJ);
         issue(gnx, gn, stg + (cur ^ 1) * HB);
       }
       cp_async_commit();

@@ -13,6 +13,7 @@
 // and beta neighbours outside the grid skipped; the P strongest local maxima
 // in that order are kept.  One CTA per particle compacts the local maxima
 // into shared memory and selects P of them by P block-wide argmax rounds.
+#include <algorithm>
 #include <float.h>
 #include <limits.h>
 #include "internal.cuh"
@@ -1194,6 +1195,331 @@ size_t soft_warps_smem(const Plan &p) {
          4 * (capc + 32 + 4) + 16;
 }
 
+// Register-tiled chunked variant (32-bit plans, soft_n % 4 == 0): the pass
+// structure of k_soft_chunk (KB new beta slices per pass into a ring of KB+2,
+// then the local maxima of KB slices), with every phase cut into exactly as
+// many work items as the CTA has threads for L0 = 8, K = 2 (324 threads: 324
+// pairs, 324 (slice, m, 4 gamma) items, 324 4x4 (alpha, gamma) tiles, 324
+// quads of the maximum filter and of the test), and the two DFT stages on
+// packed FP32x2 operations fed by operand tables laid out in pairs:
+//   stage 2: (Re, Im) G_m(j..j+3) += S_mn (e^{i n g_j}), S read as
+//            (Re, Re, Im, Im), twiddles as (cos x4, sin x4, -sin x4);
+//   stage 3: C(i..i+3, j..j+3) += A[c][i] B[c][j], A read as pairs (a, a).
+// Each grid value is the same chain of roundings as in k_soft_chunk (the same
+// fused multiply-adds in the same order; x*(-y) equals (-x)*y exactly), so the
+// grid, the candidates and their order are bit-identical to it.  The 3x3
+// (alpha, gamma) maximum is taken separably over a thread's quad of gamma
+// values.  The bandwidth and the grid size are compile-time constants (the
+// stage loops unroll); local maxima that cannot enter the best-P list (once
+// it holds P_b entries, those that do not precede its last one) are not
+// queued for the merge.
+template <int KB, int L0, int ns>
+__global__ void __launch_bounds__(384, 2)
+k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_base,
+            const float *__restrict__ soft_d, const int *__restrict__ pair_off0, long nc0,
+            const float *__restrict__ tw, int P_max, const int *__restrict__ P_per,
+            float *__restrict__ grid_out, int *__restrict__ idx_out, double *__restrict__ euler_out,
+            double *__restrict__ score_out, int *__restrict__ n_cand_out) {
+  constexpr int NR = KB + 2;
+  const long b = blockIdx.x;
+  static_assert(ns % 4 == 0, "gamma quads");
+  constexpr int W = 2 * L0 + 1, M1 = L0 + 1, np0 = M1 * M1, n2 = ns * ns, q4 = ns / 4;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  constexpr int capc = KB * ((ns + 1) / 2) * ((ns + 1) / 2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto al4 = [](long x) { return (x + 3) & ~3L; };
+  float *ring = reinterpret_cast<float *>(smem_raw);  // [NR][n2]
+  float *mx = ring + al4(NR * n2);                     // [NR][n2] 3x3 (alpha, gamma) maxima
+  float *G = mx + al4(NR * n2);                        // [KB+1][2 M1][ns]: rows (Re, Im) of G_m
+  float *Eg = G + al4((KB + 1) * 2 * M1 * ns);         // [W][q4][12]: cos, sin, -sin of 4 gammas
+  float *Ad = Eg + al4(W * q4 * 12);                   // [2 M1][ns][2]: (a, a)
+  float *cst = Ad + al4(2 * M1 * ns * 2);              // [nc0][4] staged c, l <= L0
+  const long sdn = al4(max((long)(KB + 1) * M1 * W * 4, 2L * capc));
+  float *Sd = cst + al4(4 * nc0);                      // [KB+1][M1][W][4]: (Re, Re, Im, Im)
+  float *cv = Sd;                                      // [capc] candidates (alias of Sd)
+  int *ci = reinterpret_cast<int *>(Sd + capc);        // [capc]
+  float *rv = Sd + sdn;                                // [32]
+  int *ri = reinterpret_cast<int *>(rv + 32);          // [32]
+  int *counters = ri + 32;                             // [0] pass count, [1] kept
+  struct CDiv {  // division by a compile-time constant
+    int d;
+    __device__ __forceinline__ int div(int x) const { return x / d; }
+  };
+  constexpr CDiv dnp0{np0}, dl{M1}, dq4{q4}, dmq{M1 * q4}, dqq{q4 * q4}, dnq{ns * q4};
+  for (int t = tid; t < W * q4 * 4; t += NT) {
+    const int n = t / (q4 * 4), r = t - n * q4 * 4, j = 4 * (r >> 2) + (r & 3);
+    int tt = ((n - L0) * j) % ns;
+    if (tt < 0) tt += ns;
+    float *e = Eg + (n * q4 + (r >> 2)) * 12 + (r & 3);
+    e[0] = tw[2 * tt];
+    e[4] = tw[2 * tt + 1];
+    e[8] = -tw[2 * tt + 1];
+  }
+  for (int t = tid; t < 2 * M1 * ns; t += NT) {
+    const int cc = t / ns, i = t - cc * ns, m = cc >> 1;
+    const int tt = (m * i) % ns;
+    const float wgt = m == 0 ? 1.f : 2.f;
+    const float v = (cc & 1) ? -wgt * tw[2 * tt + 1] : wgt * tw[2 * tt];
+    Ad[2 * t] = v;
+    Ad[2 * t + 1] = v;
+  }
+  {
+    const float *cg = c + 4 * b * nc;
+    for (int t = tid; t < np0 * M1; t += NT) {
+      int q = dl.div(t), e = t - q * M1;
+      int m = isqrt_floor(q);
+      if (e <= L0 - m) {
+        const float *src = cg + pair_base[q] + 8L * e;
+        float *dst = cst + 4L * (pair_off0[q] + e);
+        dst[0] = src[0]; dst[1] = src[2]; dst[2] = src[4]; dst[3] = src[6];
+      }
+    }
+  }
+  int Pb = P_per ? min(P_per[b], P_max) : P_max;
+  if (Pb < 0) Pb = 0;
+  if (tid < 32) { rv[tid] = 0; ri[tid] = INT_MAX; }
+  if (tid == 0) counters[1] = 0;
+  __syncthreads();
+  int done = 0;  // slices [0, done) computed
+  for (int k0 = 0; k0 < ns; k0 += KB) {
+    const int hi = min(ns, k0 + KB + 1), ka = done, nk = hi - ka;
+    // phase 1: beta transform of slices ka..hi-1 into the rows m >= 0 of S
+    for (int t = tid; t < nk * np0; t += NT) {
+      int kk = dnp0.div(t), q = t - kk * np0, k = ka + kk;
+      int m = isqrt_floor(q), n = q - m * m - m;
+      const float *cp = cst + 4L * pair_off0[q];
+      const float *dp = soft_d + (long)k * nc0 + pair_off0[q];
+      float ar = 0, ai = 0, br = 0, bi = 0;
+      for (int l = m; l <= L0; ++l) {
+        float d = dp[l - m];
+        const float4 e = *reinterpret_cast<const float4 *>(cp + 4 * (l - m));
+        ar = fmaf(e.x, d, ar); ai = fmaf(e.y, d, ai);
+        br = fmaf(e.z, d, br); bi = fmaf(e.w, d, bi);
+      }
+      if ((m - n) & 1) { br = -br; bi = -bi; }  // d^l_nm = (-1)^{m-n} d^l_mn
+      float *S = Sd + (long)kk * M1 * W * 4;
+      *reinterpret_cast<float4 *>(S + 4 * (m * W + n + L0)) = make_float4(ar, ar, ai, ai);
+      if (n != m && n != -m) {
+        if (n >= 0) *reinterpret_cast<float4 *>(S + 4 * (n * W + m + L0)) = make_float4(br, br, bi, bi);
+        if (n <= 0) *reinterpret_cast<float4 *>(S + 4 * (-n * W - m + L0)) = make_float4(br, br, -bi, -bi);
+      }
+    }
+    __syncthreads();
+    // phase 2: G_m(j) = sum_n S_mn e^{i n g_j}, items (slice, m, 4 gammas)
+    for (int t = tid; t < nk * M1 * q4; t += NT) {
+      int kk = dmq.div(t), r = t - kk * M1 * q4;
+      int m = dq4.div(r), jb = r - m * q4;
+      const float *row = Sd + ((long)kk * M1 + m) * W * 4;
+      const float *e = Eg + jb * 12;
+      float2 re01 = make_float2(0.f, 0.f), re23 = re01, im01 = re01, im23 = re01;
+#pragma unroll
+      for (int n = 0; n < W; ++n, e += q4 * 12) {
+        const float4 s = *reinterpret_cast<const float4 *>(row + 4 * n);
+        const float4 er = *reinterpret_cast<const float4 *>(e);
+        const float4 ei = *reinterpret_cast<const float4 *>(e + 4);
+        const float4 ne = *reinterpret_cast<const float4 *>(e + 8);
+        const float2 sr = make_float2(s.x, s.y), si = make_float2(s.z, s.w);
+        re01 = __ffma2_rn(sr, make_float2(er.x, er.y), __ffma2_rn(si, make_float2(ne.x, ne.y), re01));
+        re23 = __ffma2_rn(sr, make_float2(er.z, er.w), __ffma2_rn(si, make_float2(ne.z, ne.w), re23));
+        im01 = __ffma2_rn(sr, make_float2(ei.x, ei.y), __ffma2_rn(si, make_float2(er.x, er.y), im01));
+        im23 = __ffma2_rn(sr, make_float2(ei.z, ei.w), __ffma2_rn(si, make_float2(er.z, er.w), im23));
+      }
+      float *Gk = G + ((long)kk * 2 * M1 + 2 * m) * ns + 4 * jb;
+      *reinterpret_cast<float4 *>(Gk) = make_float4(re01.x, re01.y, re23.x, re23.y);
+      *reinterpret_cast<float4 *>(Gk + ns) = make_float4(im01.x, im01.y, im23.x, im23.y);
+    }
+    __syncthreads();
+    // phase 3: C(i, k, j) = sum_c A[c][i] B[c][j]; 4 x 4 tiles
+    for (int t = tid; t < nk * q4 * q4; t += NT) {
+      int kk = dqq.div(t), r = t - kk * q4 * q4;
+      int iq = dq4.div(r), i0 = iq * 4, j0 = (r - iq * q4) * 4;
+      const float *Bk = G + (long)kk * 2 * M1 * ns + j0;
+      const float *Ai = Ad + 2 * i0;
+      float2 o[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u][0] = o[u][1] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int cc = 0; cc < 2 * M1; ++cc) {
+        const float4 bv = *reinterpret_cast<const float4 *>(Bk + cc * ns);
+        const float4 a01 = *reinterpret_cast<const float4 *>(Ai + 2 * cc * ns);
+        const float4 a23 = *reinterpret_cast<const float4 *>(Ai + 2 * cc * ns + 4);
+        const float2 b01 = make_float2(bv.x, bv.y), b23 = make_float2(bv.z, bv.w);
+        const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                             make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          o[u][0] = __ffma2_rn(a[u], b01, o[u][0]);
+          o[u][1] = __ffma2_rn(a[u], b23, o[u][1]);
+        }
+      }
+      float *dst = ring + ((ka + kk) % NR) * n2 + i0 * ns + j0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        *reinterpret_cast<float4 *>(dst + u * ns) = make_float4(o[u][0].x, o[u][0].y, o[u][1].x, o[u][1].y);
+    }
+    __syncthreads();
+    // 3x3 maxima over (alpha, gamma), both wrapping, of the new slices; a NaN
+    // anywhere in the window makes the maximum NaN.  Item (slice, alpha row,
+    // quad of gammas): the gamma maximum of three rows, then across rows.
+    for (int t = tid; t < nk * ns * q4; t += NT) {
+      const int kk = dnq.div(t), r = t - kk * ns * q4;
+      const int i = dq4.div(r), j0 = (r - i * q4) * 4;
+      const float *sl = ring + ((ka + kk) % NR) * n2;
+      const int jm = j0 == 0 ? ns - 1 : j0 - 1, jp = j0 + 4 == ns ? 0 : j0 + 4;
+      float m4[4];
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di < 0 ? ns - 1 : (i + di == ns ? 0 : i + di);
+        const float *rw = sl + ii * ns;
+        const float4 x = *reinterpret_cast<const float4 *>(rw + j0);
+        const float xm = rw[jm], xp = rw[jp];
+        const float c01 = nan_max(x.x, x.y), c12 = nan_max(x.y, x.z), c23 = nan_max(x.z, x.w);
+        const float r0 = nan_max(xm, c01), r1 = nan_max(c01, x.z), r2 = nan_max(c12, x.w),
+                    r3 = nan_max(c23, xp);
+        if (di == -1) { m4[0] = r0; m4[1] = r1; m4[2] = r2; m4[3] = r3; }
+        else {
+          m4[0] = nan_max(m4[0], r0); m4[1] = nan_max(m4[1], r1);
+          m4[2] = nan_max(m4[2], r2); m4[3] = nan_max(m4[3], r3);
+        }
+      }
+      *reinterpret_cast<float4 *>(mx + ((ka + kk) % NR) * n2 + i * ns + j0) =
+          make_float4(m4[0], m4[1], m4[2], m4[3]);
+    }
+    done = hi;
+    if (tid == 0) counters[0] = 0;
+    __syncthreads();
+    const int k1 = min(ns, k0 + KB), nt_ = k1 - k0;
+    if (grid_out) {
+      float *go = grid_out + b * (long)ns * n2;
+      for (int t = tid; t < nt_ * n2; t += NT) {
+        int kk = t / n2, r = t - kk * n2;
+        int i = r / ns, j = r - i * ns, k = k0 + kk;
+        go[((long)i * ns + k) * ns + j] = ring[(k % NR) * n2 + r];
+      }
+    }
+    // local maxima of slices k0..k1-1: the 3x3x3 maximum (slices outside the
+    // beta range skipped) rules out every point below it; a point equal to it
+    // takes the exact test, which also orders equal values by index
+    const bool full = counters[1] >= Pb;
+    const float thv = full && Pb > 0 ? rv[Pb - 1] : 0.f;
+    const int thi = full && Pb > 0 ? ri[Pb - 1] : 0;
+    for (int t = tid; t < ns * q4 && !(full && Pb == 0); t += NT) {
+      const int i = dq4.div(t), j0 = (t - i * q4) * 4, r = i * ns + j0;
+      int slot = k0 % NR;
+      const int prev = slot == 0 ? NR - 1 : slot - 1;
+      const float4 ninf = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+      float4 mprev = k0 > 0 ? *reinterpret_cast<const float4 *>(mx + prev * n2 + r) : ninf;
+      float4 mcur = *reinterpret_cast<const float4 *>(mx + slot * n2 + r);
+      for (int k = k0; k < k1; ++k) {
+        const int next = slot == NR - 1 ? 0 : slot + 1;
+        const float4 mnext = k < ns - 1 ? *reinterpret_cast<const float4 *>(mx + next * n2 + r) : ninf;
+        const float4 v4 = *reinterpret_cast<const float4 *>(ring + slot * n2 + r);
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+        const float m3[4] = {nan_max(nan_max(mprev.x, mcur.x), mnext.x),
+                             nan_max(nan_max(mprev.y, mcur.y), mnext.y),
+                             nan_max(nan_max(mprev.z, mcur.z), mnext.z),
+                             nan_max(nan_max(mprev.w, mcur.w), mnext.w)};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (vv[u] != m3[u]) continue;
+          const float v = vv[u];
+          const int j = j0 + u;
+          const int p = (i * ns + k) * ns + j;
+          if (full && !precedes(v, p, thv, thi)) continue;
+          bool ok = true;
+          for (int dk = -1; dk <= 1 && ok; ++dk) {
+            int kq = k + dk;
+            if (kq < 0 || kq >= ns) continue;
+            const float *sl = ring + (kq % NR) * n2;
+            for (int di = -1; di <= 1 && ok; ++di) {
+              int ii = i + di; ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
+              for (int dj = -1; dj <= 1; ++dj) {
+                if (!di && !dk && !dj) continue;
+                int jj = j + dj; jj = jj < 0 ? jj + ns : (jj >= ns ? jj - ns : jj);
+                int q = (ii * ns + kq) * ns + jj;
+                if (!precedes(v, p, sl[ii * ns + jj], q)) { ok = false; break; }
+              }
+            }
+          }
+          if (ok) {
+            int pos = atomicAdd(&counters[0], 1);
+            if (pos < capc) { cv[pos] = v; ci[pos] = p; }
+          }
+        }
+        mprev = mcur; mcur = mnext; slot = next;
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {  // warp 0: insert into the sorted best-P list
+      const int lane = tid;
+      float myv = rv[lane];
+      int myi = ri[lane];
+      int kept = counters[1];
+      const int cnt = min(counters[0], capc);
+      for (int e = 0; e < cnt; ++e) {
+        float v = cv[e];
+        int i = ci[e];
+        bool before = lane < kept && precedes(myv, myi, v, i);
+        int pos = __popc(__ballot_sync(0xffffffffu, before));
+        float upv = __shfl_up_sync(0xffffffffu, myv, 1);
+        int upi = __shfl_up_sync(0xffffffffu, myi, 1);
+        if (pos < Pb) {
+          if (lane > pos) { myv = upv; myi = upi; }
+          if (lane == pos) { myv = v; myi = i; }
+          kept = min(kept + 1, Pb);
+        }
+      }
+      rv[lane] = myv;
+      ri[lane] = myi;
+      if (lane == 0) counters[1] = kept;
+    }
+    __syncthreads();
+  }
+  const int kept = counters[1];
+  for (int r = tid; r < P_max; r += NT) {
+    long o = b * P_max + r;
+    if (r < kept) {
+      int i = ri[r];
+      idx_out[o] = i;
+      score_out[o] = (double)rv[r];
+      int ia = i / (ns * ns), kb = (i / ns) % ns, jg = i % ns;
+      euler_out[3 * o] = 2.0 * M_PI * ia / ns;
+      euler_out[3 * o + 1] = M_PI * (2.0 * kb + 1.0) / (2.0 * ns);
+      euler_out[3 * o + 2] = 2.0 * M_PI * jg / ns;
+    } else {
+      idx_out[o] = -1;
+      score_out[o] = __longlong_as_double(0x7ff8000000000000LL);
+      euler_out[3 * o] = euler_out[3 * o + 1] = euler_out[3 * o + 2] = 0.0;
+    }
+  }
+  if (tid == 0) n_cand_out[b] = kept;
+}
+
+constexpr int TILE_KB = 4;
+
+// Shared memory of k_soft_tile (the layout carved at its start).
+size_t soft_tile_smem(const Plan &p) {
+  auto al4 = [](size_t x) { return (x + 3) & ~size_t(3); };
+  const size_t W = 2 * p.L0 + 1, M1 = p.L0 + 1, ns = p.ns, n2 = ns * ns, q4 = ns / 4;
+  const size_t capc = (size_t)TILE_KB * ((ns + 1) / 2) * ((ns + 1) / 2);
+  const size_t sdn = al4(std::max((TILE_KB + 1) * M1 * W * 4, 2 * capc));
+  return 4 * (2 * al4((TILE_KB + 2) * n2) + al4((TILE_KB + 1) * 2 * M1 * ns) + al4(W * q4 * 12) +
+              al4(2 * M1 * ns * 2) + al4(4 * (size_t)p.nc0) + sdn + 32 + 32 + 4);
+}
+
+// Threads of k_soft_tile: one per 4x4 tile of a pass (324 at L0 = 8, K = 2),
+// at least 128 and at most 384.
+int soft_tile_threads(const Plan &p) {
+  const int q4 = p.ns / 4;
+  return std::min(384, std::max(128, TILE_KB * q4 * q4));
+}
+
+// Instantiated for L0 = 8, K = 2 (36 points per angle), the SOFFT of every
+// 32-bit workload here; other plans take the chunked kernel.
+bool soft_tile_ok(const Plan &p) {
+  return !p.fp64 && p.L0 == 8 && p.ns == 36 && soft_tile_smem(p) <= 113 * 1024;
+}
+
 size_t soft_chunk_smem(const Plan &p, size_t ts) {
   size_t W = 2 * p.L0 + 1, n2 = (size_t)p.ns * p.ns;
   size_t capc = (size_t)SOFT_KB * ((p.ns + 1) / 2) * ((p.ns + 1) / 2);
@@ -1217,7 +1543,7 @@ bool soft_warps_ok(const Plan &p);
 
 bool soft_grid_optional(const Plan &p) {
   const size_t ts = p.fp64 ? 8 : 4;
-  return soft_warps_ok(p) || soft_chunk_smem(p, ts) <= 227 * 1024 - 1024 || soft_stream_smem(p, ts) <= 227 * 1024 - 1024 ||
+  return soft_tile_ok(p) || soft_warps_ok(p) || soft_chunk_smem(p, ts) <= 227 * 1024 - 1024 || soft_stream_smem(p, ts) <= 227 * 1024 - 1024 ||
          (!p.fp64 && soft_fused_ok(p));
 }
 
@@ -1247,6 +1573,15 @@ cudaError_t launch_soft(const Plan &p, const T *c, int B, const int *P_per, T *g
     cudaFuncSetAttribute(k_soft_warps<SOFT_NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_soft_warps<SOFT_NW><<<B, SOFT_NW * 32, smem, st>>>(
         (const float *)c, p.nc, p.L0, p.ns, p.pair_base, (const float *)p.soft_d, p.pair_off0,
+        p.nc0, (const float *)p.soft_tw, p.P, P_per, (float *)grid, idx, euler, score, n_cand);
+    return cudaGetLastError();
+  }
+  // the register-tiled kernel unless another was chosen (bit-identical to the chunked one)
+  if (sizeof(T) == 4 && (p.tune_soft == 0 || p.tune_soft == 3) && soft_tile_ok(p)) {
+    const size_t smem = soft_tile_smem(p);
+    cudaFuncSetAttribute(k_soft_tile<TILE_KB, 8, 36>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_soft_tile<TILE_KB, 8, 36><<<B, soft_tile_threads(p), smem, st>>>(
+        (const float *)c, p.nc, p.pair_base, (const float *)p.soft_d, p.pair_off0,
         p.nc0, (const float *)p.soft_tw, p.P, P_per, (float *)grid, idx, euler, score, n_cand);
     return cudaGetLastError();
   }

@@ -1,7 +1,8 @@
 """The SOFFT search kernels of the 32-bit plans are interchangeable tile
-choices: the chunked kernel and the warp-per-slice kernel give bit-identical
-grids, candidates and refined results (FP32 and TF32 plans, fixed and
-per-particle candidate counts), and the autotuner may pick either."""
+choices: the chunked kernel, the warp-per-slice kernel and the register-tiled
+kernel give bit-identical grids, candidates and refined results (FP32 and TF32
+plans, fixed and per-particle candidate counts), and the autotuner may pick
+any of them."""
 import dataclasses
 
 import pytest
@@ -31,18 +32,19 @@ def test_soft_kernels_bit_identical(name, prec):
     h = m.matcha_analyze(plan, d["templates"])
     c = m.matcha_correlate_coeffs(plan, f, h, 1)
     outs = []
-    for k in (1, 2):
+    for k in (1, 2, 3):
         plan.set_tiles(soft_kernel=k)
         soft = m.matcha_soft_search(plan, c, P_per=P_per)
         al = m.matcha_align(plan, d["particles"], d["templates"], P_per=P_per)
         torch.cuda.synchronize()
         outs.append((soft, al))
-    (s1, a1), (s2, a2) = outs
     same = lambda a, b: torch.testing.assert_close(a, b, rtol=0, atol=0, equal_nan=True)
-    for key in ("grid", "idx", "score", "euler", "n_cand"):   # scores past n_cand are NaN
-        same(s1[key], s2[key])
-    for key in ("euler", "R", "score", "best_p", "flags"):
-        same(a1[key], a2[key])
+    s1, a1 = outs[0]
+    for s2, a2 in outs[1:]:
+        for key in ("grid", "idx", "score", "euler", "n_cand"):   # scores past n_cand are NaN
+            same(s1[key], s2[key])
+        for key in ("euler", "R", "score", "best_p", "flags"):
+            same(a1[key], a2[key])
     plan.close()
 
 
@@ -52,10 +54,12 @@ def test_autotuner_reports_the_soft_kernel():
     plan = m.plan_for_workload(w, precision=m.FP32)
     rep = plan.autotune(d["particles"], d["templates"])
     print("autotune:", rep)
-    assert rep["soft_kernel"] in (1, 2) and min(rep["soft_ms"]) > 0
+    assert rep["soft_kernel"] in (1, 2, 3) and min(rep["soft_ms"]) > 0
     plan64 = m.plan_for_workload(w, precision=m.FP64)
     with pytest.raises(m.MatchaError):
         plan64.set_tiles(soft_kernel=2)     # the warp kernel serves the 32-bit plans only
+    with pytest.raises(m.MatchaError):
+        plan64.set_tiles(soft_kernel=3)     # so does the register-tiled kernel
 
 
 @pytest.mark.parametrize("name,prec,B", [("var48", m.FP32, 200), ("batch64", m.FP32, 300),
