@@ -39,7 +39,7 @@ struct Plan {
   void *phi_cs;                 // real [np][2]: cos, sin (2 pi k / n_phi)
   void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout
-  void *rcoef;                  // real, grouped layout: (a, -b, -e, 0) of the step l -> l+1
+  void *rcoef;                  // real, grouped layout: (a, -b, -e) of the step l -> l+1, -l(l+1)
   void *seedK;                  // real [ngroups][4]: (sqrt(binom(2m, m+n)) of both halves, 0, 0)
   void *dft_cs;                 // real [2][2][Qf][Mq]: folded phi-DFT table (parity, cos|sin, q, column)
   int Mp;                       // orders padded to a multiple of 4

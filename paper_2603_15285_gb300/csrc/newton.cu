@@ -4,7 +4,11 @@
 // C_L(a,b,g) = Re sum_{l<=L} sum_{m,n} c^l_{mn} e^{i(m a + n g)} d^l_{mn}(b),
 // grad and Hessian in (a, b, g): d/da brings i m, d/dg brings i n, d/db acts
 // on d^l (Appendix A.4).  Every evaluation runs the three-term l-recurrence
-// of d, d' and d'' for each order pair (m, n) with m >= |n| and uses
+// of d and d' for each order pair (m, n) with m >= |n|; the second
+// derivative comes from the differential equation of the Wigner functions,
+//   d'' = -cot(b) d' + ((m^2 + n^2 - 2mn cos b) / sin^2 b - l(l+1)) d,
+// applied to the sums over l (the plans with the rescaled 32-bit recurrence
+// above L_J = 64 run a third recurrence for d'' instead).  It uses
 //   d^l_{nm} = (-1)^{m-n} d^l_{mn}            (transposed image),
 //   term(-m,-n) = conj(term(m,n))              (real volumes),
 // so one recurrence serves the four orders (m,n), (n,m), (-m,-n), (-n,-m).
@@ -169,7 +173,7 @@ struct GroupWalk {
 // Staging buffer of one sub-slot, per half (double buffering), in reals:
 // [4] seed norms (K_a, K_b, 0, 0), then per degree entry 16 reals: the 8 c
 // reals of the group entry, then its 8 recurrence reals (a_a, a_b, -b_a,
-// -b_b, -e_a, -e_b, 0, 0); L_J + 1 entries.
+// -b_b, -e_a, -e_b, -l(l+1), -l(l+1)); L_J + 1 entries.
 __host__ __device__ __forceinline__ int stage_half(int LJ) { return 4 + 16 * (LJ + 1); }
 
 // Per-candidate tables, candidate index fastest with an odd stride
@@ -191,7 +195,7 @@ __host__ __device__ __forceinline__ int cand_stride(int P) { return P | 1; }
 // sh^ba in the padded power tables; a term whose integer coefficient is zero
 // may read a zero pad, so it adds exactly 0.  z: bytes between consecutive
 // powers in the table.
-template <typename T, bool FULL>
+template <typename T, bool FULL, bool ODE = false>
 __device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, unsigned z, v2<T> K, int aa,
                                            int ba, v2<T> &D0, v2<T> &D1, v2<T> &D2) {
   T c0, c1, s0, sm1;
@@ -211,6 +215,7 @@ __device__ __forceinline__ void group_seed(unsigned pc, unsigned ps, unsigned z,
     const v2<T> t1 = vmul(B, vmul(vset<T>(c1, c2), vset<T>(sm1, sm2)));
     const v2<T> t2 = vmul(A, vmul(vset<T>(cm1, c0), vset<T>(s1, s0)));
     D1 = vmul(vmul(GK, vset<T>(T(0.5), T(0.5))), vfma(t2, mone, t1));
+    if (ODE) return;  // d'' comes from the differential equation
     // b(b-1) ch^{a+2} sh^{b-2} - (b(a+1) + a(b+1)) ch^a sh^b + a(a-1) ch^{a-2} sh^{b+2}
     const v2<T> u1 = vmul(vmul(B, vadd(B, mone)), vmul(vset<T>(c2, c3), vset<T>(sm2, sm3)));
     const v2<T> u2 = vmul(vfma(B, vadd(A, one), vmul(A, vadd(B, one))), pp0);
@@ -304,13 +309,14 @@ __device__ __forceinline__ void group_seed_rs(unsigned pc, unsigned ps, unsigned
   }
 }
 
-// One staged degree entry of a partner group: c of both halves, and the
-// recurrence coefficients (a, -b, -e) of the step to the next degree.
+// One staged degree entry of a partner group: c of both halves, the
+// recurrence coefficients (a, -b, -e) of the step to the next degree, and
+// -l(l+1) of the entry's own degree l.
 template <typename T> struct Coef {
   v2<T> CR, CI, DR, DI;
 };
 template <typename T> struct Rec {
-  v2<T> A, NB, NE;
+  v2<T> A, NB, NE, NL;
 };
 template <typename T> __device__ __forceinline__ void load_coef(unsigned a, Coef<T> &e) {
   lds4(a, e.CR, e.CI);
@@ -318,9 +324,10 @@ template <typename T> __device__ __forceinline__ void load_coef(unsigned a, Coef
 }
 template <typename T> __device__ __forceinline__ void load_rec(unsigned a, Rec<T> &r) {
   lds4(a + 8 * sizeof(T), r.A, r.NB);
-  lds2(a + 12 * sizeof(T), r.NE);
+  lds4(a + 12 * sizeof(T), r.NE, r.NL);
 }
-// Z += c d (and c d', c d'' when FULL) for one entry.
+// Z += c d (and c d', c d'' when FULL) for one entry; with ODE the third
+// sums take -l(l+1) c d (passed as D2 = -l(l+1) d) instead of c d''.
 template <typename T, bool FULL>
 __device__ __forceinline__ void accumulate(const Coef<T> &e, const v2<T> &D0, const v2<T> &D1,
                                            const v2<T> &D2, v2<T> (&Z)[12]) {
@@ -336,13 +343,16 @@ __device__ __forceinline__ void accumulate(const Coef<T> &e, const v2<T> &D0, co
 // One recurrence step from (d^l, d^{l-1}) = (D, P); d^{l+1} overwrites P:
 //   d^{l+1} = t d - e p,  t = a x - b,
 //   d'^{l+1} = t d' - a s d - e p',  d''^{l+1} = t d'' - 2 a s d' - a x d - e p''.
-template <typename T, bool FULL>
+template <typename T, bool FULL, bool ODE = false>
 __device__ __forceinline__ void step_into(const Rec<T> &r, v2<T> X, v2<T> NS, v2<T> NX,
                                           const v2<T> &D0, const v2<T> &D1, const v2<T> &D2,
                                           v2<T> &P0, v2<T> &P1, v2<T> &P2) {
   const v2<T> t = vfma(r.A, X, r.NB);
   P0 = vfma(t, D0, vmul(r.NE, P0));
-  if (FULL) {
+  if (FULL && ODE) {
+    const v2<T> nAs = vmul(r.A, NS);
+    P1 = vfma(t, D1, vfma(nAs, D0, vmul(r.NE, P1)));
+  } else if (FULL) {
     const v2<T> nAs = vmul(r.A, NS);
     P1 = vfma(t, D1, vfma(nAs, D0, vmul(r.NE, P1)));
     const v2<T> nAx = vmul(r.A, NX);
@@ -352,12 +362,14 @@ __device__ __forceinline__ void step_into(const Rec<T> &r, v2<T> X, v2<T> NS, v2
 
 // Sums over l = m..m+last of one partner group for one candidate: Z[0..3] =
 // sum d (Re c_mn, Im c_mn, Re c_nm, Im c_nm), then the same with d' (Z[4..7])
-// and d'' (Z[8..11]) when FULL; each a pair over the two halves.  a: shared
-// address of the group's first staged entry (16 reals per entry).  The loop
-// takes two degrees per trip with the roles of (D, P) swapped in the second;
-// c is loaded one degree ahead of its use, the step coefficients at the start
-// of their degree.
-template <typename T, bool FULL>
+// and d'' (Z[8..11]) when FULL; each a pair over the two halves.  With ODE
+// the second-derivative recurrence is not run: Z[8..11] gets -l(l+1) d in
+// place of d'' (the caller completes it with the differential equation).
+// a: shared address of the group's first staged entry (16 reals per entry).
+// The loop takes two degrees per trip with the roles of (D, P) swapped in the
+// second; c is loaded one degree ahead of its use, the step coefficients at
+// the start of their degree.
+template <typename T, bool FULL, bool ODE = false>
 __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> NS, v2<T> NX,
                                           v2<T> D0, v2<T> D1, v2<T> D2, v2<T> (&Z)[12]) {
   constexpr unsigned ES = 16 * sizeof(T);
@@ -365,6 +377,11 @@ __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> N
   v2<T> P0 = zero, P1 = zero, P2 = zero;
 #pragma unroll
   for (int q = 0; q < 12; ++q) Z[q] = zero;
+  auto acc = [&](const Coef<T> &e, const v2<T> &S0, const v2<T> &S1, const v2<T> &S2,
+                 const v2<T> &NL) {
+    if (ODE) accumulate<T, FULL>(e, S0, S1, vmul(NL, S0), Z);
+    else accumulate<T, FULL>(e, S0, S1, S2, Z);
+  };
   Coef<T> e0, e1;
   Rec<T> r;
   load_coef(a, e0);
@@ -372,21 +389,24 @@ __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> N
   for (; i + 2 <= last; i += 2, a += 2 * ES) {
     load_rec(a, r);
     load_coef(a + ES, e1);
-    accumulate<T, FULL>(e0, D0, D1, D2, Z);
-    step_into<T, FULL>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+    acc(e0, D0, D1, D2, r.NL);
+    step_into<T, FULL, ODE>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
     load_rec(a + ES, r);
     load_coef(a + 2 * ES, e0);
-    accumulate<T, FULL>(e1, P0, P1, P2, Z);
-    step_into<T, FULL>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
+    acc(e1, P0, P1, P2, r.NL);
+    step_into<T, FULL, ODE>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
   }
+  v2<T> nl = zero;
   if (i < last) {  // degrees i (with a step) and last = i + 1
     load_rec(a, r);
     load_coef(a + ES, e1);
-    accumulate<T, FULL>(e0, D0, D1, D2, Z);
-    step_into<T, FULL>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
-    accumulate<T, FULL>(e1, P0, P1, P2, Z);
+    acc(e0, D0, D1, D2, r.NL);
+    step_into<T, FULL, ODE>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+    if (ODE && FULL) lds2(a + ES + 14 * sizeof(T), nl);
+    acc(e1, P0, P1, P2, nl);
   } else {         // degree last = i
-    accumulate<T, FULL>(e0, D0, D1, D2, Z);
+    if (ODE && FULL) lds2(a + 14 * sizeof(T), nl);
+    acc(e0, D0, D1, D2, nl);
   }
 }
 
@@ -582,6 +602,20 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   const int pc = p < P ? p : 0;
   const T xb = evp[8 * pc], sb = evp[8 * pc + 1];
   const v2<T> X = vset<T>(xb, xb), NS = vset<T>(-sb, -sb), NX = vset<T>(-xb, -xb);
+  // constants of the differential equation for d'' (the non-rescaled path):
+  // 1/sin^2 b and -cot b with sin b floored away from zero, and the pole form
+  // of the numerator of Q (sign of n in m -/+ n, and +4 sin^2(b/2) or -4 cos^2(b/2))
+  v2<T> IS2, NCOT, QSG, QC4;
+  {
+    const T sfl = sizeof(T) == 8 ? T(1e-150) : T(1e-18);
+    const T se = sb > sfl ? sb : sfl;
+    const T is2 = T(1) / (se * se), ncot = -xb / se;
+    const T chb = evp[8 * pc + 2], shb = evp[8 * pc + 3];
+    const bool north = xb >= T(0);
+    const T sg = north ? T(-1) : T(1), c4 = north ? T(4) * shb * shb : T(-4) * chb * chb;
+    IS2 = vset<T>(is2, is2); NCOT = vset<T>(ncot, ncot);
+    QSG = vset<T>(sg, sg); QC4 = vset<T>(c4, c4);
+  }
   // shared addresses of this candidate's tables (index 0 of each row)
   const unsigned zs = z * PS;  // bytes between consecutive positions of a row
   const unsigned pcu = smem_u32(pw + PW_PAD * PS + pc);
@@ -646,8 +680,18 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
                               D2, E0, E1);
           group_sum_rs<FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, E0, E1, Z);
         } else {
-          group_seed<T, FULL>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
-          group_sum<T, FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+          group_seed<T, FULL, true>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
+          group_sum<T, FULL, true>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+          if (FULL) {
+            // d'' = -cot(b) d' + (Q - l(l+1)) d with Q = (m^2 + n^2 - 2mn cos b) / sin^2 b,
+            // the numerator as (m - n)^2 + 4mn sin^2(b/2) (beta <= pi/2) or
+            // (m + n)^2 - 4mn cos^2(b/2) (beta > pi/2), free of cancellation at the pole
+            const v2<T> mm = vset<T>(T(m), T(m)), nh = vset<T>(T(na), T(na + 1));
+            const v2<T> dd = vfma(nh, QSG, mm);
+            const v2<T> Q = vmul(vfma(vmul(mm, nh), QC4, vmul(dd, dd)), IS2);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Z[8 + k] = vfma(NCOT, Z[4 + k], vfma(Q, Z[k], Z[8 + k]));
+          }
         }
         const T fm = T(m), fa = T(na);
         const v2<T> MM = vset<T>(fm, fm), NN = vset<T>(fa, fa + T(1));

@@ -108,7 +108,7 @@ __global__ void k_rcoef(int L, int npairs, const int *pair_base, double *rc) {
       }
     }
     double *o = rc + pair_base[q] + 8L * (l - m);
-    o[0] = a; o[2] = -b; o[4] = -e; o[6] = 0;
+    o[0] = a; o[2] = -b; o[4] = -e; o[6] = -(double)l * (l + 1);  // -l(l+1): the d'' equation
     if (n == m) { o[1] = 0; o[3] = 0; o[5] = 0; o[7] = 0; }
   }
 }

@@ -1359,31 +1359,37 @@ k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_b
     }
     __syncthreads();
     // 3x3 maxima over (alpha, gamma), both wrapping, of the new slices; a NaN
-    // anywhere in the window makes the maximum NaN.  Item (slice, alpha row,
-    // quad of gammas): the gamma maximum of three rows, then across rows.
-    for (int t = tid; t < nk * ns * q4; t += NT) {
-      const int kk = dnq.div(t), r = t - kk * ns * q4;
-      const int i = dq4.div(r), j0 = (r - i * q4) * 4;
+    // anywhere in the window makes the maximum NaN.  Item (slice, block of 4
+    // alpha rows, quad of 4 gammas): the gamma maxima of the 6 rows i0-1..i0+4
+    // from 16-byte reads of the quad and its two neighbours, then the maxima
+    // over 3 consecutive rows.
+    for (int t = tid; t < nk * q4 * q4; t += NT) {
+      const int kk = dqq.div(t), r = t - kk * q4 * q4;
+      const int ib = dq4.div(r), jq = r - ib * q4, i0 = 4 * ib, j0 = 4 * jq;
       const float *sl = ring + ((ka + kk) % NR) * n2;
-      const int jm = j0 == 0 ? ns - 1 : j0 - 1, jp = j0 + 4 == ns ? 0 : j0 + 4;
-      float m4[4];
+      const int jl = (jq == 0 ? q4 - 1 : jq - 1) * 4, jr = (jq == q4 - 1 ? 0 : jq + 1) * 4;
+      float rm[6][4];
 #pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        const int ii = i + di < 0 ? ns - 1 : (i + di == ns ? 0 : i + di);
+      for (int di = 0; di < 6; ++di) {
+        int ii = i0 - 1 + di;
+        ii = ii < 0 ? ii + ns : (ii >= ns ? ii - ns : ii);
         const float *rw = sl + ii * ns;
         const float4 x = *reinterpret_cast<const float4 *>(rw + j0);
-        const float xm = rw[jm], xp = rw[jp];
-        const float c01 = nan_max(x.x, x.y), c12 = nan_max(x.y, x.z), c23 = nan_max(x.z, x.w);
-        const float r0 = nan_max(xm, c01), r1 = nan_max(c01, x.z), r2 = nan_max(c12, x.w),
-                    r3 = nan_max(c23, xp);
-        if (di == -1) { m4[0] = r0; m4[1] = r1; m4[2] = r2; m4[3] = r3; }
-        else {
-          m4[0] = nan_max(m4[0], r0); m4[1] = nan_max(m4[1], r1);
-          m4[2] = nan_max(m4[2], r2); m4[3] = nan_max(m4[3], r3);
-        }
+        const float xm = reinterpret_cast<const float4 *>(rw + jl)->w;
+        const float xp = reinterpret_cast<const float4 *>(rw + jr)->x;
+        rm[di][0] = nan_max(nan_max(xm, x.x), x.y);
+        rm[di][1] = nan_max(nan_max(x.x, x.y), x.z);
+        rm[di][2] = nan_max(nan_max(x.y, x.z), x.w);
+        rm[di][3] = nan_max(nan_max(x.z, x.w), xp);
       }
-      *reinterpret_cast<float4 *>(mx + ((ka + kk) % NR) * n2 + i * ns + j0) =
-          make_float4(m4[0], m4[1], m4[2], m4[3]);
+      float *mo = mx + ((ka + kk) % NR) * n2 + i0 * ns + j0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float m4[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) m4[v] = nan_max(nan_max(rm[u][v], rm[u + 1][v]), rm[u + 2][v]);
+        *reinterpret_cast<float4 *>(mo + u * ns) = make_float4(m4[0], m4[1], m4[2], m4[3]);
+      }
     }
     done = hi;
     if (tid == 0) counters[0] = 0;
