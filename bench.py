@@ -279,7 +279,8 @@ def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
     T0 = (w.L0 + 1) * (2 * w.L0 + 1) * (2 * w.L0 + 3) // 3
     soft_flops = (4.0 * n * T0 + 2.5 * n ** 3 * math.log2(n * n)) * B
     sp = alu_peak
-    out["soft"] = {"kernel": "k_soft_chunk", "bound": "alu",
+    tiled = prec != m.FP64 and w.L0 == 8 and n == 36  # the register-tiled kernel's plans
+    out["soft"] = {"kernel": "k_soft_tile" if tiled else "k_soft_chunk", "bound": "alu",
                    "unit": "TFLOP/s", "peak": sp,
                    "flops_per_particle": soft_flops / B,
                    "achieved": soft_flops / (stage_ms["soft"] * 1e-3) / 1e12,
@@ -655,7 +656,7 @@ def main():
     H = plan.handle
     stages = ["analyze", "correlate", "soft", "newton", "select"]
     # Kernels of one matcha_align step: per part of the batch k_analyze2 x2
-    # (particles, templates), the contraction, k_soft_chunk (grid and top-P
+    # (particles, templates), the contraction, k_soft_tile (grid and top-P
     # fused), k_newton, k_final_select; from 256 particles on the batch runs as
     # min(4, B / 128) concurrent parts (a shared template is analysed once).
     n_parts = 1 if B < 256 else min(4, B // 128)  # (batch64's SOFFT is fused)

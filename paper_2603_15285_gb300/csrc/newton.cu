@@ -79,7 +79,7 @@ struct SmemLayout {
   double *th, *tr, *del, *Cc, *res;
   void *red;  // [warps][P][10] working precision
   int *state, *steps, *tries, *fl;
-  void *evp, *ea, *pw, *stage;
+  void *ea, *pw, *stage;
 };
 
 // Asynchronous global -> shared copies (no registers involved).
@@ -520,21 +520,11 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   constexpr unsigned z = sizeof(T);
   const int P = A.P, cpw = A.cpw, LJ = A.LJ;
   const int NPW = pw_row(LJ), RW = ph_row(LJ), PS = cand_stride(P);
-  T *evp = (T *)sm.evp;  // [P][8]: x, s, ch, sh, cos a, sin a, cos g, sin g
   T *ph = (T *)sm.ea;    // [4][RW][PS]: cos k a, sin k a, cos k g, sin k g
   T *pw = (T *)sm.pw;    // [2][NPW][PS]: PW_PAD zeros, then ch^k (sh^k), k = 0..2LJ+3
   const int tid = threadIdx.x;
-  // per candidate: (cos, sin) of beta, beta/2, alpha, gamma, one angle per thread
-  for (int t = tid; t < 4 * P; t += blockDim.x) {
-    const int p = t >> 2, a = t & 3;
-    if (need[p]) {
-      const double *q = pts + 3 * p;
-      const T x = a == 0 ? (T)q[1] : a == 1 ? (T)q[1] * T(0.5) : (T)q[a == 2 ? 0 : 2];
-      evp[8 * p + 2 * a] = tcos(x);
-      evp[8 * p + 2 * a + 1] = tsin(x);
-    }
-  }
-  __syncthreads();
+  // Each thread takes the cosines and sines it needs from the point itself
+  // (no table and no barrier before the tables below).
   // powers k = 0..2L+3 of cos(beta/2) and sin(beta/2): runs of 8 consecutive
   // powers per item, the first by binary powering, the rest by one product each
   constexpr int RUN = 8;
@@ -544,7 +534,8 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
     int pr = dw.div(t), k0 = (t - pr * nrun) * RUN;
     int p = pr >> 1, which = pr & 1;
     if (!need[p]) continue;
-    const T x = evp[8 * p + 2 + which];
+    const T hb = (T)pts[3 * p + 1] * T(0.5);
+    const T x = which ? tsin(hb) : tcos(hb);
     const int k1 = min(k0 + RUN, npk);
     if (RS) {  // mantissa rows, then exponent rows (2 NPW rows further on)
       for (int k = k0; k < k1; ++k) {
@@ -571,7 +562,8 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   for (int t = tid; t < 16 * P; t += blockDim.x) {
     const int pq = t >> 3, q = t & 7, p = pq >> 1, which = pq & 1;
     if (need[p]) {
-      const T c1 = evp[8 * p + 4 + 2 * which], s1 = evp[8 * p + 5 + 2 * which];
+      const T ang = (T)pts[3 * p + 2 * which];  // alpha or gamma
+      const T c1 = tcos(ang), s1 = tsin(ang);
       T *cr_ = ph + ((2 * which) * RW + LJ) * PS + p, *ci_ = cr_ + RW * PS;
       // e^{2ix}, e^{4ix}, e^{8ix} and e^{iqx} by binary powering
       const T c2 = c1 * c1 - s1 * s1, s2 = T(2) * c1 * s1;
@@ -600,7 +592,8 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   const unsigned submask = cpw == 32 ? 0xffffffffu : (((1u << cpw) - 1u) << (sub * cpw));
   const bool act = p < P && need[p];
   const int pc = p < P ? p : 0;
-  const T xb = evp[8 * pc], sb = evp[8 * pc + 1];
+  const T bt = (T)pts[3 * pc + 1];
+  const T xb = tcos(bt), sb = tsin(bt);
   const v2<T> X = vset<T>(xb, xb), NS = vset<T>(-sb, -sb), NX = vset<T>(-xb, -xb);
   // constants of the differential equation for d'' (the non-rescaled path):
   // 1/sin^2 b and -cot b with sin b floored away from zero, and the pole form
@@ -610,7 +603,7 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
     const T sfl = sizeof(T) == 8 ? T(1e-150) : T(1e-18);
     const T se = sb > sfl ? sb : sfl;
     const T is2 = T(1) / (se * se), ncot = -xb / se;
-    const T chb = evp[8 * pc + 2], shb = evp[8 * pc + 3];
+    const T chb = tcos(bt * T(0.5)), shb = tsin(bt * T(0.5));
     const bool north = xb >= T(0);
     const T sg = north ? T(-1) : T(1), c4 = north ? T(4) * shb * shb : T(-4) * chb * chb;
     IS2 = vset<T>(is2, is2); NCOT = vset<T>(ncot, ncot);
@@ -882,7 +875,6 @@ __device__ __forceinline__ int *carve_smem(unsigned char *smem_raw, int P, int L
   u = (u + 15) & ~uintptr_t(15);
   T *tp = reinterpret_cast<T *>(u);
   sm.red = tp; tp += 10 * P * NEWTON_WARPS;
-  sm.evp = tp; tp += 8 * P;
   sm.ea = tp; tp += 4 * cand_stride(P) * ph_row(LJ);
   sm.pw = tp; tp += (RS ? 4 : 2) * cand_stride(P) * pw_row(LJ);
   tp = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(tp) + 31) & ~uintptr_t(31));
@@ -1103,7 +1095,7 @@ static size_t newton_smem_bytes(const Plan &p, size_t tsize, int slots) {
   bytes += sizeof(int) * 5 * P;
   bytes = (bytes + 15) / 16 * 16;
   const size_t PS = cand_stride(p.P);
-  bytes += tsize * (10 * P * NEWTON_WARPS + 8 * P + 4 * PS * ph_row(p.LJ) + pw_rows * PS * pw_row(p.LJ)) + 32;
+  bytes += tsize * (10 * P * NEWTON_WARPS + 4 * PS * ph_row(p.LJ) + pw_rows * PS * pw_row(p.LJ)) + 32;
   bytes += tsize * (size_t)slots * 2 * stage_half(p.LJ);
   return bytes;
 }
