@@ -10,6 +10,8 @@
 // samples into shared memory, folds the real DFT (pairs k, n_phi - k) and
 // runs the Legendre sums against the plan's table.
 #include <stdlib.h>
+#include <algorithm>
+#include <type_traits>
 #include "internal.cuh"
 
 namespace matcha {
@@ -145,12 +147,18 @@ __device__ __forceinline__ void st2(T *p, typename Vec2<T>::type v) {
   *reinterpret_cast<typename Vec2<T>::type *>(p) = v;
 }
 
-template <typename T, int G>
+// TEX: the four x-y corners of each plane of a trilinear cell come from one
+// 2x2 texture gather on the 2-D view (x, z N + y) of the volume (texture
+// views of runs of ta.vpt volumes); the gathered values are the voxels
+// themselves (no filtering), so the samples are bit-identical to the
+// eight-load path, and the gathers go through the texture pipe, which serves
+// the 2x2 footprints faster than eight scattered loads.
+template <typename T, int G, bool TEX>
 __global__ void __launch_bounds__(256)
 k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const double *__restrict__ rs, const double *__restrict__ xj, const T *__restrict__ phi_cs,
            const T *__restrict__ dcs, int Mp, int Qf, int Mq, const T *__restrict__ ptabT,
-           const T *__restrict__ ring, T *__restrict__ out) {
+           const T *__restrict__ ring, T *__restrict__ out, const __grid_constant__ TexArgs ta) {
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
   const int Gs = G;  // the launcher picks G dividing S
@@ -187,6 +195,13 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   __syncthreads();
   const T c0 = (T)(0.5 * N);
   const T hi = (T)(N - 1);
+  cudaTextureObject_t tob = 0;
+  float yoff = 0.f;  // first row of this volume in its texture view
+  if (TEX) {
+    const int run = (int)(b / ta.vpt);
+    tob = ta.t[run];
+    yoff = (float)((b - (long)run * ta.vpt) * NN);
+  }
   // trilinear at (px, py, pz); corners clamped so that all eight are in the box
   // when the point is (the value is unchanged), bounds-checked otherwise
   auto sample = [&](T px, T py, T pz) -> T {
@@ -195,10 +210,20 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     if (inside) {
       int i = min((int)fx, N - 2), j = min((int)fy, N - 2), k = min((int)fz, N - 2);
       T tx = px - (T)i, ty = py - (T)j, tz = pz - (T)k;
-      const float *v = vol + ((long)k * N + j) * N + i;
-      T v000 = (T)__ldg(v), v001 = (T)__ldg(v + 1), v010 = (T)__ldg(v + N), v011 = (T)__ldg(v + N + 1);
-      T v100 = (T)__ldg(v + NN), v101 = (T)__ldg(v + NN + 1), v110 = (T)__ldg(v + NN + N),
+      T v000, v001, v010, v011, v100, v101, v110, v111;
+      if (TEX) {
+        // gather components: x (i, j+1), y (i+1, j+1), z (i+1, j), w (i, j)
+        const float tx0 = (float)i + 1.f, ty0 = yoff + (float)(k * N + j) + 1.f;
+        const float4 q0 = tex2Dgather<float4>(tob, tx0, ty0, 0);
+        const float4 q1 = tex2Dgather<float4>(tob, tx0, ty0 + (float)N, 0);
+        v000 = (T)q0.w; v001 = (T)q0.z; v010 = (T)q0.x; v011 = (T)q0.y;
+        v100 = (T)q1.w; v101 = (T)q1.z; v110 = (T)q1.x; v111 = (T)q1.y;
+      } else {
+        const float *v = vol + ((long)k * N + j) * N + i;
+        v000 = (T)__ldg(v); v001 = (T)__ldg(v + 1); v010 = (T)__ldg(v + N); v011 = (T)__ldg(v + N + 1);
+        v100 = (T)__ldg(v + NN); v101 = (T)__ldg(v + NN + 1); v110 = (T)__ldg(v + NN + N);
         v111 = (T)__ldg(v + NN + N + 1);
+      }
       T a00 = v000 + tx * (v001 - v000), a01 = v010 + tx * (v011 - v010);
       T a10 = v100 + tx * (v101 - v100), a11 = v110 + tx * (v111 - v110);
       T b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
@@ -350,6 +375,76 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
   }
 }
 
+// Texture views for a batch (looked up in, or added to, the plan's cache).
+// False when the batch does not qualify (row pitch or base alignment, view
+// height, more than TEX_MAX views) or when a new view would have to be made
+// while `st` is being captured into a graph; the kernel then reads the
+// volumes with plain loads.  Evicting a view synchronises the device first
+// (a kernel still queued may use it).
+bool texture_views(const Plan &p, const float *vols, int B, cudaStream_t st, TexArgs &ta) {
+  ta.vpt = 1;
+  int dev = 0, pitch_al = 0, tex_al = 0, max_w = 0, max_h = 0, max_pitch = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&pitch_al, cudaDevAttrTexturePitchAlignment, dev);
+  cudaDeviceGetAttribute(&tex_al, cudaDevAttrTextureAlignment, dev);
+  cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, dev);
+  cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DLinearHeight, dev);
+  cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxTexture2DLinearPitch, dev);
+  const long N = p.N, NN = N * N, pitch = 4 * N, vbytes = 4 * N * NN;
+  if (pitch_al <= 0 || tex_al <= 0 || pitch % pitch_al || pitch > max_pitch || N > max_w ||
+      NN > max_h || vbytes % tex_al || reinterpret_cast<uintptr_t>(vols) % tex_al)
+    return false;
+  const int vpt = (int)std::min<long>(B, max_h / NN), ntex = (B + vpt - 1) / vpt;
+  if (ntex > TEX_MAX) return false;
+  TexSet *hit = nullptr, *slot = nullptr;
+  for (auto &t : p.texsets) {
+    if (t.ntex && t.base == vols && t.B == B && t.vpt == vpt) hit = &t;
+    if (!slot || !t.ntex || (slot->ntex && t.used < slot->used)) slot = &t;
+  }
+  if (!hit) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return false;
+    if (slot->ntex) {
+      cudaDeviceSynchronize();
+      for (int i = 0; i < slot->ntex; ++i) cudaDestroyTextureObject(slot->t[i]);
+      slot->ntex = 0;
+    }
+    for (int r = 0; r < ntex; ++r) {
+      cudaResourceDesc rd = {};
+      rd.resType = cudaResourceTypePitch2D;
+      rd.res.pitch2D.devPtr = const_cast<float *>(vols) + (size_t)r * vpt * N * NN;
+      rd.res.pitch2D.desc = cudaCreateChannelDesc<float>();
+      rd.res.pitch2D.width = N;
+      rd.res.pitch2D.height = (size_t)std::min(vpt, B - r * vpt) * NN;
+      rd.res.pitch2D.pitchInBytes = pitch;
+      cudaTextureDesc td = {};
+      td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      if (cudaCreateTextureObject(&slot->t[r], &rd, &td, nullptr) != cudaSuccess) {
+        for (int i = 0; i < r; ++i) cudaDestroyTextureObject(slot->t[i]);
+        cudaGetLastError();
+        return false;
+      }
+    }
+    slot->base = vols; slot->B = B; slot->vpt = vpt; slot->ntex = ntex;
+    hit = slot;
+  }
+  hit->used = ++p.tex_clock;
+  for (int i = 0; i < hit->ntex; ++i) ta.t[i] = hit->t[i];
+  ta.vpt = hit->vpt;
+  return true;
+}
+
+void destroy_texsets(Plan &p) {
+  for (auto &t : p.texsets) {
+    for (int i = 0; i < t.ntex; ++i) cudaDestroyTextureObject(t.t[i]);
+    t.ntex = 0;
+  }
+}
+
 template <typename T>
 size_t analyze2_smem(const Plan &p, int G) {
   int K1 = p.np / 2 - 1, Rp = (G * p.nt + 3) / 4 * 4;
@@ -368,13 +463,19 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
     while (G > 1 && (p.S % G != 0 || analyze2_smem<T>(p, G) > 100 * 1024)) G >>= 1;
     size_t smem = analyze2_smem<T>(p, G);
     if (smem <= 200 * 1024) {
-      auto kern = G == 8 ? k_analyze2<T, 8> : G == 4 ? k_analyze2<T, 4> : G == 2 ? k_analyze2<T, 2>
-                                                                                  : k_analyze2<T, 1>;
+      TexArgs ta;
+      const bool tex = texture_views(p, vols, B, st, ta);
+      auto pick = [&](auto tag) {
+        constexpr bool X = decltype(tag)::value;
+        return G == 8 ? k_analyze2<T, 8, X> : G == 4 ? k_analyze2<T, 4, X>
+             : G == 2 ? k_analyze2<T, 2, X> : k_analyze2<T, 1, X>;
+      };
+      auto kern = tex ? pick(std::true_type{}) : pick(std::false_type{});
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<dim3(p.S / G, B), 256, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj,
                                                 (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
                                                 p.Qf, p.Mq, (const T *)p.ptab, (const T *)p.ring,
-                                                coef);
+                                                coef, ta);
       return cudaGetLastError();
     }
   }

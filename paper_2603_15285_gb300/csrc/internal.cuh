@@ -8,6 +8,23 @@
 
 namespace matcha {
 
+// Texture views of a batch of volumes for the analysis gathers: 2-D
+// pitch-linear views (x, z N + y) of runs of `vpt` consecutive volumes, so
+// one 2x2 texture gather fetches the four x-y corners of a trilinear cell in
+// one plane.  A texture object only describes the memory (it owns none), so
+// a view stays valid for any later allocation at the same address.
+constexpr int TEX_MAX = 256;  // views per batch (kernel parameter array)
+struct TexSet {
+  const void *base = nullptr;
+  int B = 0, vpt = 0, ntex = 0;
+  unsigned long long used = 0;
+  cudaTextureObject_t t[TEX_MAX] = {};
+};
+struct TexArgs {  // passed by value to the analysis kernel
+  cudaTextureObject_t t[TEX_MAX];
+  int vpt;
+};
+
 // Plan: descriptor, derived sizes and the device tables it owns.
 struct Plan {
   matcha_plan_desc desc;
@@ -62,7 +79,12 @@ struct Plan {
   static constexpr int NSPLIT = 4;
   cudaStream_t split_stream[NSPLIT - 1] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[NSPLIT - 1] = {};
+  // texture views of recently analysed batches (most recently used kept)
+  static constexpr int NTEXSET = 16;
+  mutable TexSet texsets[NTEXSET];
+  mutable unsigned long long tex_clock = 0;
 };
+void destroy_texsets(Plan &p);
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 

@@ -283,6 +283,7 @@ matcha_status matcha_plan_destroy(matcha_plan plan) {
     if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  destroy_texsets(*p);
   if (p->ball_W) cudaFree(p->ball_W);
   cudaError_t e = cudaFree(p->base);
   delete p;
