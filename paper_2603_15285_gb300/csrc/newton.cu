@@ -170,11 +170,17 @@ struct GroupWalk {
   }
 };
 
-// Staging buffer of one sub-slot, per half (double buffering), in reals:
-// [4] seed norms (K_a, K_b, 0, 0), then per degree entry 16 reals: the 8 c
-// reals of the group entry, then its 8 recurrence reals (a_a, a_b, -b_a,
-// -b_b, -e_a, -e_b, -l(l+1), -l(l+1)); L_J + 1 entries.
-__host__ __device__ __forceinline__ int stage_half(int LJ) { return 4 + 16 * (LJ + 1); }
+// Staging buffer of one sub-slot, per half (double buffering), in reals: a
+// header (below), then per degree entry 16 reals: the 8 c reals of the group
+// entry, then its 8 recurrence reals (a_a, a_b, -b_a, -b_b, -e_a, -e_b,
+// -l(l+1), -l(l+1)); L_J + 1 entries.
+// Batched staging: a half buffer takes a run of up to STAGE_BATCH consecutive
+// groups of its sub-slot whose entries fit in L_J + 1 entries; its header
+// holds 8 reals per group: (K_a, K_b, 0, 0) from the seed table, then (m,
+// n_a, first entry) written by the sub-slot's first lane, then one pad.
+constexpr int STAGE_BATCH = 4;
+constexpr int STAGE_HDR = 8 * STAGE_BATCH;  // reals
+__host__ __device__ __forceinline__ int stage_half(int LJ) { return STAGE_HDR + 16 * (LJ + 1); }
 
 // Per-candidate tables, candidate index fastest with an odd stride
 // cand_stride(P) >= P, so the lanes of a sub-slot (one candidate each) read
@@ -628,15 +634,7 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
   constexpr int CH = 16 / (int)sizeof(T), CPE = 16 / CH;  // reals per chunk, chunks per entry
   const int part = p % CPE, e0 = p / CPE, estep = cpw / CPE;
   const T *srcb = (part < CPE / 2 ? cb : rcoef) + CH * (part % (CPE / 2)) + 8 * e0;
-  const unsigned dsto = z * (4 + 16 * e0 + CH * part);
-  auto issue = [&](const Group &G, int g, unsigned hb) {
-    const int len = L - G.m + 1;
-    const T *src = srcb + 8L * G.off;
-    unsigned dst = hb + dsto;
-    for (int e = e0; e < len; e += estep, src += 8 * estep, dst += 16 * z * estep)
-      cp_async16s(dst, src);
-    if (p < 4 / CH) cp_async16s(hb + 16 * p, seedK + 4L * g + CH * p);
-  };
+  const unsigned dsto = z * (STAGE_HDR + 16 * e0 + CH * part);
   // Sub-slot `slot` takes group k * nslots + slot in even rounds k and
   // k * nslots + (nslots - 1 - slot) in odd ones: groups come in increasing g
   // (non-increasing length), so the alternating order balances the sub-slots
@@ -645,36 +643,60 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
     return k * nslots + ((k & 1) ? nslots - 1 - slot : slot);
   };
   if (slot < nslots && slot < ng) {
-    int cur = 0, k = 0;
-    int g = group_at(0);
     GroupWalk walk;
-    Group gc = walk.at(g, LJ);
-    issue(gc, g, stg);
-    cp_async_commit();
-    while (g < ng) {
-      const int gn = group_at(k + 1);
-      Group gnx = gc;
-      if (gn < ng) {
-        gnx = walk.at(gn, LJ);
-        issue(gnx, gn, stg + (cur ^ 1) * HB);
+    int k = 0;  // next group of this sub-slot's sequence
+    // Copies the next batch of groups into half buffer hb; returns its size
+    // (0 when the sub-slot has no group left).
+    auto issue_batch = [&](unsigned hb) -> int {
+      int cnt = 0, eoff = 0;
+      while (cnt < STAGE_BATCH) {
+        const int g = group_at(k);
+        if (g >= ng) break;
+        const Group G = walk.at(g, LJ);
+        const int len = L - G.m + 1;
+        if (cnt > 0 && eoff + len > LJ + 1) break;
+        const T *src = srcb + 8L * G.off;
+        unsigned dst = hb + dsto + 16 * z * eoff;
+        for (int e = e0; e < len; e += estep, src += 8 * estep, dst += 16 * z * estep)
+          cp_async16s(dst, src);
+        const unsigned hd = hb + z * 8 * cnt;
+        if (p < 4 / CH) cp_async16s(hd + 16 * p, seedK + 4L * g + CH * p);
+        if (p == 0) {
+          T *h = reinterpret_cast<T *>(__cvta_shared_to_generic(hd));
+          h[4] = T(G.m); h[5] = T(G.na); h[6] = T(eoff);
+        }
+        eoff += len;
+        ++cnt;
+        ++k;
       }
+      return cnt;
+    };
+    int cur = 0;
+    int ncur = issue_batch(stg);
+    cp_async_commit();
+    while (ncur > 0) {
+      const int nnext = issue_batch(stg + (cur ^ 1) * HB);
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp(submask);
       if (act) {
-        const int m = gc.m, na = gc.na, aa = m + na, ba = m - na;
-        const unsigned buf = stg + cur * HB;
+       for (int t = 0; t < ncur; ++t) {
+        const unsigned buf = stg + cur * HB, hd = buf + z * 8 * t;
+        T hm, hn, he;
+        lds1(hd + 4 * z, hm); lds1(hd + 5 * z, hn); lds1(hd + 6 * z, he);
+        const int m = (int)hm, na = (int)hn, eoff = (int)he, aa = m + na, ba = m - na;
+        const unsigned ent = buf + z * (STAGE_HDR + 16 * eoff);
         v2<T> K, D0, D1, D2, Z[12];
-        lds2(buf, K);
+        lds2(hd, K);
         D1 = D2 = vset<T>(T(0), T(0));
         if constexpr (RS) {
           int E0, E1;
           group_seed_rs<FULL>(pcu + zs * aa, psu + zs * ba, zs * 2 * NPW, zs, K, aa, ba, D0, D1,
                               D2, E0, E1);
-          group_sum_rs<FULL>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, E0, E1, Z);
+          group_sum_rs<FULL>(ent, L - m, X, NS, NX, D0, D1, D2, E0, E1, Z);
         } else {
           group_seed<T, FULL, true>(pcu + zs * aa, psu + zs * ba, zs, K, aa, ba, D0, D1, D2);
-          group_sum<T, FULL, true>(buf + 4 * z, L - m, X, NS, NX, D0, D1, D2, Z);
+          group_sum<T, FULL, true>(ent, L - m, X, NS, NX, D0, D1, D2, Z);
           if (FULL) {
             // d'' = -cot(b) d' + (Q - l(l+1)) d with Q = (m^2 + n^2 - 2mn cos b) / sin^2 b,
             // the numerator as (m - n)^2 + 4mn sin^2(b/2) (beta <= pi/2) or
@@ -683,7 +705,7 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
             const v2<T> dd = vfma(nh, QSG, mm);
             const v2<T> Q = vmul(vfma(vmul(mm, nh), QC4, vmul(dd, dd)), IS2);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) Z[8 + k] = vfma(NCOT, Z[4 + k], vfma(Q, Z[k], Z[8 + k]));
+            for (int q = 0; q < 4; ++q) Z[8 + q] = vfma(NCOT, Z[4 + q], vfma(Q, Z[q], Z[8 + q]));
           }
         }
         const T fm = T(m), fa = T(na);
@@ -713,12 +735,11 @@ __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__
           const v2<T> Wt = vset<T>(na == m || na == -m ? T(0) : T(2), na + 1 < m ? T(-2) : T(0));
           add_image<T, FULL>(acc, Wt, NN, MM, ER, EI, NEI, Z[2], Z[3], Z[6], Z[7], Z[10], Z[11]);
         }
+       }
       }
       __syncwarp(submask);
       cur ^= 1;
-      ++k;
-      g = gn;
-      gc = gnx;
+      ncur = nnext;
     }
     cp_async_wait<0>();
   }
