@@ -34,7 +34,11 @@ WORKLOAD = "batch64"
 # FP32 ops per Wigner recurrence step, counted from the Newton kernel source
 # (an FMA counts 2): derivative evaluation 20 (d, d', d'' recurrence) + 24
 # (12 FMA accumulations); value-only evaluation 5 + 8.
-FLOPS_FULL_STEP = 44
+# flops per (order pair, degree, candidate) step of the refinement's recurrences, counted
+# from the source: a derivative step accumulates c d, c d', -l(l+1) c d (12 flops per
+# complex pair of sums) and advances d and d' (11); a value-only step accumulates c d (8)
+# and advances d (5)
+FLOPS_FULL_STEP = 36
 FLOPS_VALUE_STEP = 13
 SMS, FP32_LANES = 152, 128
 
