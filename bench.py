@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-oracle-gate", action="store_true",
                     help="skip the oracle run over the whole batch (accuracy against the oracle)")
     ap.add_argument("--batch", type=int, default=None, help="override particles per GPU")
+    ap.add_argument("--stages", action="store_true",
+                    help="time each entry point of the path once per stage on the batch (one "
+                         "launch per stage, the SOFFT grid kept on chip) and exit: the "
+                         "command the kernel profiles are captured with")
     ap.add_argument("--paper-batch", type=int, default=256, help="particles of the 200^3 leg")
     ap.add_argument("--pose6d-batch", type=int, default=1024, help="particles of the 6-D leg")
     return ap.parse_args()
@@ -244,6 +248,17 @@ def measure_fp32_peak(st, local, reps=5):
         out[name + "_tflops"] = flops / (best * 1e-3) / 1e12
     out["clocks"] = sampler.stop()
     return out
+
+
+def survey_newton_units(w, B, newton_ms, peak):
+    """Newton's work in Wigner terms, 3 P sum_j T(L_j) per particle with
+    T(L) = (L+1)(2L+1)(2L+3)/3, at 30 flops per term (the per-unit figure of
+    the path's roofline table), against the ALU peak."""
+    T = lambda L: (L + 1) * (2 * L + 1) * (2 * L + 3) // 3
+    terms = 3 * w.P * sum(T(L) for L in w.L_sched)
+    ach = 30.0 * terms * B / (newton_ms * 1e-3) / 1e12
+    return {"wigner_terms_per_particle": terms, "flops_per_term": 30, "achieved": ach,
+            "unit": "TFLOP/s", "frac": ach / peak}
 
 
 def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
@@ -614,10 +629,75 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_stages(args):
+    """One launch per stage of the path through the C ABI on the batch (after
+    `--warmup` untimed passes), each timed with CUDA events: analysis of the
+    particles and templates, contraction, SOFFT search (allocation-free entry,
+    grid on chip), Newton march from the search's candidates, final selection."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_15285_gb300 as m
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    B = args.batch or w.B
+    prec = {"fp32": m.FP32, "fp64": m.FP64, "tf32": m.TF32, "bf16": m.BF16}[args.precision]
+    d = synth.make_batch(w, B=B, device="cuda")
+    parts, temps = d["particles"].contiguous(), d["templates"].contiguous()
+    plan = m.plan_for_workload(w, precision=prec)
+    rt = plan.real_dtype
+    f = torch.empty((B, w.n_shells, plan.info.n_lm, 2), dtype=rt, device="cuda")
+    h = torch.empty_like(f)
+    c = torch.empty((B, plan.info.corr_entries, 2, 2), dtype=rt, device="cuda")
+    L, st, H = m.lib(), torch.cuda.current_stream(), plan.handle
+    sp = st.cuda_stream
+    idx = torch.empty((B, w.P), dtype=torch.int32, device="cuda")
+    eu = torch.empty((B, w.P, 3), dtype=torch.float64, device="cuda")
+    sc = torch.empty((B, w.P), dtype=torch.float64, device="cuda")
+    fl = torch.empty((B, w.P), dtype=torch.int32, device="cuda")
+    nc = torch.empty((B,), dtype=torch.int32, device="cuda")
+    out = [torch.empty((B, k), dtype=t, device="cuda") for k, t in
+           ((3, torch.float64), (9, torch.float64), (1, torch.float64), (1, torch.int32),
+            (1, torch.int32))]
+    e0, s0 = torch.empty_like(eu), torch.empty_like(sc)
+    stages = {
+        "analyze": lambda: (m._check(L.matcha_analyze(H, parts.data_ptr(), B, f.data_ptr(), sp), "a"),
+                            m._check(L.matcha_analyze(H, temps.data_ptr(), B, h.data_ptr(), sp), "a")),
+        "correlate": lambda: m._check(L.matcha_correlate_coeffs(H, f.data_ptr(), h.data_ptr(), B, 1,
+                                                                c.data_ptr(), sp), "c"),
+        "soft": lambda: (m._check(L.matcha_soft_search_noalloc(
+            H, c.data_ptr(), B, None, idx.data_ptr(), eu.data_ptr(), sc.data_ptr(),
+            nc.data_ptr(), sp), "s"), e0.copy_(eu), s0.copy_(sc)),
+        "newton": lambda: m._check(L.matcha_newton_march(H, c.data_ptr(), B, nc.data_ptr(),
+                                                         eu.data_ptr(), sc.data_ptr(),
+                                                         fl.data_ptr(), None, sp), "n"),
+        "select": lambda: m._check(L.matcha_final_select(
+            H, B, None, nc.data_ptr(), eu.data_ptr(), sc.data_ptr(), fl.data_ptr(),
+            *[o.data_ptr() for o in out], sp), "f"),
+    }
+    res = {}
+    for name, fn in stages.items():
+        for _ in range(args.warmup):
+            if name == "newton":
+                eu.copy_(e0); sc.copy_(s0)
+            fn()
+        if name == "newton":
+            eu.copy_(e0); sc.copy_(s0)
+        a = torch.cuda.Event(enable_timing=True); z = torch.cuda.Event(enable_timing=True)
+        a.record(st); fn(); z.record(st)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(z)
+    print(json.dumps({"stages_ms": res, "particles": B, "workload": WORKLOAD,
+                      "precision": args.precision}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.stages:
+        run_stages(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -778,7 +858,11 @@ def main():
                                      "%d lanes x 2 x %.0f MHz)" % (fp32_derived, SMS, FP32_LANES, clk))
                                     if is32 else
                                     "%d SMs x 2 FP64 lanes x 2 x %.0f MHz (derived)" % (SMS, clk),
-                     "flops_per_launch": newton_flops},
+                     "flops_per_launch": newton_flops,
+                     # the same launch in the survey's algorithmic unit: 3 P sum_j T(L_j)
+                     # Wigner terms per particle (three evaluations per level) at 30 flops
+                     # per term, against the same peak
+                     "survey_units": survey_newton_units(w, B, stage_ms["newton"], peak)},
         "fp32_peak_probe": fp32_meas,
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,

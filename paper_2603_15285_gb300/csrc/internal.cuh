@@ -53,6 +53,9 @@ struct Plan {
   void *base = nullptr;
   double *rs, *wrad, *xj, *wj;  // S, S, nt, nt (FP64 always)
   void *ptab;                   // real [nt][nlm]: w_j (2 pi / n_phi) Pbar_lm(x_j)
+  void *ptab_leg;               // real [nt][nlm]: ptab with its columns in the Legendre item order
+  int *leg_lm;                  // [nlm] (l << 16) | m of Legendre item t: m ascending, then the
+                                // parity of l + m, then l (runs of equal m and parity)
   void *phi_cs;                 // real [np][2]: cos, sin (2 pi k / n_phi)
   void *soft_tw;                // real [ns][2]: cos, sin (2 pi t / ns)
   void *soft_d;                 // real [ns][nc0]: d^l_mn(beta_k) in the SOFFT layout

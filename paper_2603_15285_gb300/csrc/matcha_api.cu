@@ -187,6 +187,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   size_t o_pt = add(rs * p->nlm * p->nt), o_phi = add(rs * 2 * p->np), o_tw = add(rs * 2 * p->ns);
   size_t o_sd = add(rs * p->ns * p->nc0), o_rc = add(rs * 4 * p->nc), o_K = add(rs * 4 * p->ngroups);
   size_t o_off = add(4 * p->npairs), o_off0 = add(4 * p->npairs0);
+  size_t o_ptl = add(rs * p->nlm * p->nt), o_leg = add(4 * (size_t)p->nlm);
   size_t o_dcs = add(rs * 4 * (size_t)p->Qf * p->Mq);
   size_t o_ring = add(rs * 2 * (size_t)p->S * p->nt);
   size_t o_err = add(sizeof(int));
@@ -201,6 +202,7 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->ptab = b + o_pt; p->phi_cs = b + o_phi; p->soft_tw = b + o_tw; p->soft_d = b + o_sd;
   p->rcoef = b + o_rc; p->seedK = b + o_K;
   p->pair_base = (int *)(b + o_off); p->pair_off0 = (int *)(b + o_off0);
+  p->ptab_leg = b + o_ptl; p->leg_lm = (int *)(b + o_leg);
   p->dft_cs = b + o_dcs;
   p->ring = b + o_ring;
   p->dev_err = (int *)(b + o_err);
@@ -225,6 +227,13 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
                    rs * 2 * (size_t)p->N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_base, base.data(), 4 * p->npairs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->pair_off0, off0.data(), 4 * p->npairs0, cudaMemcpyHostToDevice);
+  {  // Legendre items: m ascending, then the parity of l + m, then l
+    std::vector<int> leg;
+    for (int m = 0; m <= p->LJ; ++m)
+      for (int par = 0; par < 2; ++par)
+        for (int l = m + par; l <= p->LJ; l += 2) leg.push_back((l << 16) | m);
+    if (e == cudaSuccess) e = cudaMemcpy(p->leg_lm, leg.data(), 4 * leg.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = build_tables(*p, 0);
   if (e != cudaSuccess) {
     cudaFree(p->base);

@@ -195,6 +195,17 @@ __global__ void k_to_float(const double *in, float *out, long n) {
   if (i < n) out[i] = (float)in[i];
 }
 
+// The Legendre table with its columns in the analysis' item order:
+// out[j][t] = in[j][lm(t)].
+template <typename T>
+__global__ void k_ptab_leg(int nt, int nlm, const int *leg, const T *in, T *out) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)nt * nlm) return;
+  const int j = (int)(t / nlm), c = (int)(t - (long)j * nlm);
+  const int l = leg[c] >> 16, m = leg[c] & 0xffff;
+  out[t] = in[(long)j * nlm + l * (l + 1) / 2 + m];
+}
+
 cudaError_t build_tables(Plan &p, cudaStream_t st) {
   // scratch for the FP64 versions of the real tables
   size_t n_ptab = (size_t)p.nlm * p.nt, n_phi = 2 * (size_t)p.np, n_tw = 2 * (size_t)p.ns;
@@ -236,6 +247,15 @@ cudaError_t build_tables(Plan &p, cudaStream_t st) {
         {dcs, p.dft_cs, n_dcs}, {ring, p.ring, n_ring}};
     for (auto &c : cp)
       k_to_float<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c.src, (float *)c.dst, (long)c.n);
+  }
+  {
+    const unsigned nb = (unsigned)((n_ptab + 255) / 256);
+    if (p.fp64)
+      k_ptab_leg<double><<<nb, 256, 0, st>>>(p.nt, p.nlm, p.leg_lm, (const double *)p.ptab,
+                                               (double *)p.ptab_leg);
+    else
+      k_ptab_leg<float><<<nb, 256, 0, st>>>(p.nt, p.nlm, p.leg_lm, (const float *)p.ptab,
+                                              (float *)p.ptab_leg);
   }
   e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(st);
