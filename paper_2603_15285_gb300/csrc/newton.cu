@@ -380,9 +380,7 @@ __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> N
                                           v2<T> D0, v2<T> D1, v2<T> D2, v2<T> (&Z)[12]) {
   constexpr unsigned ES = 16 * sizeof(T);
   const v2<T> zero = vset<T>(T(0), T(0));
-  v2<T> P0 = zero, P1 = zero, P2 = zero;
-#pragma unroll
-  for (int q = 0; q < 12; ++q) Z[q] = zero;
+  v2<T> P0, P1 = zero, P2 = zero;
   auto acc = [&](const Coef<T> &e, const v2<T> &S0, const v2<T> &S1, const v2<T> &S2,
                  const v2<T> &NL) {
     if (ODE) accumulate<T, FULL>(e, S0, S1, vmul(NL, S0), Z);
@@ -391,28 +389,59 @@ __device__ __forceinline__ void group_sum(unsigned a, int last, v2<T> X, v2<T> N
   Coef<T> e0, e1;
   Rec<T> r;
   load_coef(a, e0);
-  int i = 0;
+  load_rec(a, r);
+  // degree m: the sums start from its products (a product rounds as the
+  // multiply-add onto zero does)
+  {
+    const v2<T> S2 = ODE ? vmul(r.NL, D0) : D2;
+    Z[0] = vmul(e0.CR, D0); Z[1] = vmul(e0.CI, D0); Z[2] = vmul(e0.DR, D0); Z[3] = vmul(e0.DI, D0);
+    if (FULL) {
+      Z[4] = vmul(e0.CR, D1); Z[5] = vmul(e0.CI, D1); Z[6] = vmul(e0.DR, D1); Z[7] = vmul(e0.DI, D1);
+      Z[8] = vmul(e0.CR, S2); Z[9] = vmul(e0.CI, S2); Z[10] = vmul(e0.DR, S2); Z[11] = vmul(e0.DI, S2);
+    } else {
+#pragma unroll
+      for (int q = 4; q < 12; ++q) Z[q] = zero;
+    }
+  }
+  if (last == 0) return;
+  // the step from degree m, whose predecessor state is zero
+  {
+    const v2<T> t = vfma(r.A, X, r.NB);
+    P0 = vmul(t, D0);
+    if (FULL) {
+      const v2<T> nAs = vmul(r.A, NS);
+      P1 = vfma(t, D1, vmul(nAs, D0));
+      if (!ODE) {
+        const v2<T> nAx = vmul(r.A, NX);
+        P2 = vfma(t, D2, vfma(vadd(nAs, nAs), D1, vmul(nAx, D0)));
+      }
+    }
+  }
+  a += ES;
+  load_coef(a, e1);
+  // two degrees per trip: degree i in (P0, P1, P2), degree i + 1 in (D0, D1, D2)
+  int i = 1;
   for (; i + 2 <= last; i += 2, a += 2 * ES) {
     load_rec(a, r);
-    load_coef(a + ES, e1);
-    acc(e0, D0, D1, D2, r.NL);
-    step_into<T, FULL, ODE>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
-    load_rec(a + ES, r);
-    load_coef(a + 2 * ES, e0);
+    load_coef(a + ES, e0);
     acc(e1, P0, P1, P2, r.NL);
     step_into<T, FULL, ODE>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
+    load_rec(a + ES, r);
+    load_coef(a + 2 * ES, e1);
+    acc(e0, D0, D1, D2, r.NL);
+    step_into<T, FULL, ODE>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
   }
   v2<T> nl = zero;
   if (i < last) {  // degrees i (with a step) and last = i + 1
     load_rec(a, r);
-    load_coef(a + ES, e1);
-    acc(e0, D0, D1, D2, r.NL);
-    step_into<T, FULL, ODE>(r, X, NS, NX, D0, D1, D2, P0, P1, P2);
+    load_coef(a + ES, e0);
+    acc(e1, P0, P1, P2, r.NL);
+    step_into<T, FULL, ODE>(r, X, NS, NX, P0, P1, P2, D0, D1, D2);
     if (ODE && FULL) lds2(a + ES + 14 * sizeof(T), nl);
-    acc(e1, P0, P1, P2, nl);
+    acc(e0, D0, D1, D2, nl);
   } else {         // degree last = i
     if (ODE && FULL) lds2(a + 14 * sizeof(T), nl);
-    acc(e0, D0, D1, D2, nl);
+    acc(e1, P0, P1, P2, nl);
   }
 }
 
