@@ -1246,6 +1246,15 @@ k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_b
     __device__ __forceinline__ int div(int x) const { return x / d; }
   };
   constexpr CDiv dnp0{np0}, dl{M1}, dq4{q4}, dmq{M1 * q4}, dqq{q4 * q4}, dnq{ns * q4};
+  // (row, quad) of item r of a rows x q4 grid: the first q4 - 1 quads of every
+  // row first, eight consecutive items per row, then the last quad of each row,
+  // so that the eight lanes of a 16-byte shared access stay in one row
+  // (conflict-free) instead of straddling two
+  auto split = [](int r, int rows, int &row, int &quad) {
+    constexpr int Q = q4 - 1;
+    if (r < Q * rows) { row = r / Q; quad = r - row * Q; }
+    else { row = r - Q * rows; quad = Q; }
+  };
   for (int t = tid; t < W * q4 * 4; t += NT) {
     const int n = t / (q4 * 4), r = t - n * q4 * 4, j = 4 * (r >> 2) + (r & 3);
     int tt = ((n - L0) * j) % ns;
@@ -1307,8 +1316,8 @@ k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_b
     __syncthreads();
     // phase 2: G_m(j) = sum_n S_mn e^{i n g_j}, items (slice, m, 4 gammas)
     for (int t = tid; t < nk * M1 * q4; t += NT) {
-      int kk = dmq.div(t), r = t - kk * M1 * q4;
-      int m = dq4.div(r), jb = r - m * q4;
+      int kk = dmq.div(t), r = t - kk * M1 * q4, m, jb;
+      split(r, M1, m, jb);
       const float *row = Sd + ((long)kk * M1 + m) * W * 4;
       const float *e = Eg + jb * 12;
       float2 re01 = make_float2(0.f, 0.f), re23 = re01, im01 = re01, im23 = re01;
@@ -1331,8 +1340,9 @@ k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_b
     __syncthreads();
     // phase 3: C(i, k, j) = sum_c A[c][i] B[c][j]; 4 x 4 tiles
     for (int t = tid; t < nk * q4 * q4; t += NT) {
-      int kk = dqq.div(t), r = t - kk * q4 * q4;
-      int iq = dq4.div(r), i0 = iq * 4, j0 = (r - iq * q4) * 4;
+      int kk = dqq.div(t), r = t - kk * q4 * q4, iq, jq;
+      split(r, q4, iq, jq);
+      const int i0 = iq * 4, j0 = jq * 4;
       const float *Bk = G + (long)kk * 2 * M1 * ns + j0;
       const float *Ai = Ad + 2 * i0;
       float2 o[4][2];
@@ -1365,7 +1375,9 @@ k_soft_tile(const float *__restrict__ c, long nc, const int *__restrict__ pair_b
     // over 3 consecutive rows.
     for (int t = tid; t < nk * q4 * q4; t += NT) {
       const int kk = dqq.div(t), r = t - kk * q4 * q4;
-      const int ib = dq4.div(r), jq = r - ib * q4, i0 = 4 * ib, j0 = 4 * jq;
+      int ib, jq;
+      split(r, q4, ib, jq);
+      const int i0 = 4 * ib, j0 = 4 * jq;
       const float *sl = ring + ((ka + kk) % NR) * n2;
       const int jl = (jq == 0 ? q4 - 1 : jq - 1) * 4, jr = (jq == q4 - 1 ? 0 : jq + 1) * 4;
       float rm[6][4];
