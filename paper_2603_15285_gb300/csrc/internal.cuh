@@ -62,7 +62,7 @@ struct Plan {
   void *rcoef;                  // real, grouped layout: (a, -b, -e) of the step l -> l+1, -l(l+1)
   void *seedK;                  // real [ngroups][4]: (sqrt(binom(2m, m+n)) of both halves, 0, 0)
   void *dft_cs;                 // real [2][2][Qf][Mq]: folded phi-DFT table (parity, cos|sin, q, column)
-  int Mp;                       // orders padded to a multiple of 4
+  int Mp;                       // analysis F row: orders padded to a multiple of 4, plus 1
   int Qf, Mq;                   // folded DFT rows ceil(L_J/2); columns per order parity, padded to 4
   void *ring;                   // real [S * nt][2]: (r_s sin t_j, N/2 + r_s cos t_j) of ring s * nt + j
   void *fft_tw;                 // real [N][2]: cos, sin (-2 pi j / N), the box FFT's twiddles

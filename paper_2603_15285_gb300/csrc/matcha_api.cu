@@ -140,7 +140,10 @@ matcha_status matcha_plan_create(const matcha_plan_desc *d, matcha_plan *out) {
   p->npairs = (p->LJ + 1) * (p->LJ + 1);
   p->npairs0 = (p->L0 + 1) * (p->L0 + 1);
   p->ns = 2 * p->K * (p->L0 + 1);
-  p->Mp = (p->LJ + 1 + 3) / 4 * 4;
+  // F rows of the analysis: the orders padded to a multiple of 4, plus one, so
+  // that the 4-ring x 4-order tiles' stores of consecutive ring quads fall in
+  // different banks (an even row stride of 4 Mp complex values would repeat them)
+  p->Mp = (p->LJ + 1 + 3) / 4 * 4 + 1;
   p->Qf = (p->LJ + 1) / 2;
   p->Mq = (p->LJ / 2 + 1 + 3) / 4 * 4;
   p->ngroups = (p->LJ + 1) * (p->LJ + 2) / 2;

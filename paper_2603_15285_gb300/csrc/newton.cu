@@ -18,9 +18,10 @@
 // p of a sub-slot follows candidate p.  A sub-slot walks partner groups (the
 // two order pairs (m, n), (m, n+1) of one m, stored interleaved), and each
 // lane advances both pairs of a group with paired (FP32x2 / 2 x FP64)
-// operations, so every lane reads its own copy of c^l and of the recurrence
-// coefficients from shared memory (staged per group with cp.async); nothing
-// is broadcast.  Per-lane partial sums are reduced in a fixed order (the two
+// operations: c^l, the recurrence coefficients and the recurrence state are
+// pairs over the two partners, so no packed operand is a broadcast pair.  The
+// entries are staged in shared memory with cp.async, in batches of up to four
+// consecutive groups of the sub-slot.  Per-lane partial sums are reduced in a fixed order (the two
 // halves, shuffles across sub-slots, then warps in index order), all in the
 // plan's working precision and converted to FP64 at the end, so results do
 // not depend on scheduling.
@@ -544,10 +545,11 @@ __device__ __forceinline__ void phase(v2<T> Ar, v2<T> Ai, v2<T> Gr, v2<T> Gi, v2
 // need[p] != 0; results in res[p][0..9] (FP64).  Called by the whole CTA.
 //
 // Lane layout: a warp holds 32 / cpw sub-slots of cpw lanes; lane p of a
-// sub-slot follows candidate p.  Sub-slot `slot` walks the partner groups
-// g = slot, slot + nslots, ... of bandwidth L; the next group's entries are
-// copied into the other half of the slot's buffer while the current one is
-// summed, so every shared-memory read in the l-loop is a broadcast.
+// sub-slot follows candidate p.  Sub-slot `slot` walks the partner groups of
+// bandwidth L in its alternating order; the next batch of its groups is
+// copied into the other half of the slot's buffer while the current batch is
+// summed, and the lanes of a sub-slot read the same staged entries (one
+// shared-memory broadcast per load).
 template <typename T, bool FULL, bool RS>
 __device__ __forceinline__ void evaluate(const NewtonArgs &A, int L, const T *__restrict__ cb,
                                          const T *__restrict__ rcoef, const T *__restrict__ seedK,
