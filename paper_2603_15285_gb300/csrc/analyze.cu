@@ -160,6 +160,8 @@ __device__ __forceinline__ void st4(T *p, const T (&v)[4]) {
 // eight-load path, and the gathers go through the texture pipe, which serves
 // the 2x2 footprints faster than eight scattered loads.
 constexpr int ANALYZE_THREADS = 192;
+// samples whose texture gathers are in flight together (per thread)
+template <typename T> struct GatherBatch { static constexpr int value = sizeof(T) == 4 ? 2 : 2; };
 
 template <typename T, int G, bool TEX>
 __global__ void __launch_bounds__(ANALYZE_THREADS)
@@ -168,6 +170,7 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const T *__restrict__ dcs, int Mp, int Qf, int Mq, const T *__restrict__ ptabT,
            const int *__restrict__ leg, const T *__restrict__ ring, T *__restrict__ out,
            const __grid_constant__ TexArgs ta) {
+  constexpr int GB = GatherBatch<T>::value;
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
   const int Gs = G;  // the launcher picks G dividing S
@@ -206,6 +209,16 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     tob = ta.t[run];
     yoff = (float)((b - (long)run * ta.vpt) * NN);
   }
+  // trilinear combination of the two gathered planes (components: x (i, j+1),
+  // y (i+1, j+1), z (i+1, j), w (i, j)) at cell offsets (tx, ty, tz)
+  auto combine = [](const float4 &q0, const float4 &q1, T tx, T ty, T tz) -> T {
+    const T v000 = (T)q0.w, v001 = (T)q0.z, v010 = (T)q0.x, v011 = (T)q0.y;
+    const T v100 = (T)q1.w, v101 = (T)q1.z, v110 = (T)q1.x, v111 = (T)q1.y;
+    T a00 = v000 + tx * (v001 - v000), a01 = v010 + tx * (v011 - v010);
+    T a10 = v100 + tx * (v101 - v100), a11 = v110 + tx * (v111 - v110);
+    T b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
+    return b0 + tz * (b1 - b0);
+  };
   // trilinear at (px, py, pz); corners clamped so that all eight are in the box
   // when the point is (the value is unchanged), bounds-checked otherwise
   auto sample = [&](T px, T py, T pz) -> T {
@@ -214,15 +227,14 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     if (inside) {
       int i = min((int)fx, N - 2), j = min((int)fy, N - 2), k = min((int)fz, N - 2);
       T tx = px - (T)i, ty = py - (T)j, tz = pz - (T)k;
-      T v000, v001, v010, v011, v100, v101, v110, v111;
       if (TEX) {
-        // gather components: x (i, j+1), y (i+1, j+1), z (i+1, j), w (i, j)
         const float tx0 = (float)i + 1.f, ty0 = yoff + (float)(k * N + j) + 1.f;
         const float4 q0 = tex2Dgather<float4>(tob, tx0, ty0, 0);
         const float4 q1 = tex2Dgather<float4>(tob, tx0, ty0 + (float)N, 0);
-        v000 = (T)q0.w; v001 = (T)q0.z; v010 = (T)q0.x; v011 = (T)q0.y;
-        v100 = (T)q1.w; v101 = (T)q1.z; v110 = (T)q1.x; v111 = (T)q1.y;
-      } else {
+        return combine(q0, q1, tx, ty, tz);
+      }
+      T v000, v001, v010, v011, v100, v101, v110, v111;
+      {
         const float *v = vol + ((long)k * N + j) * N + i;
         v000 = (T)__ldg(v); v001 = (T)__ldg(v + 1); v010 = (T)__ldg(v + N); v011 = (T)__ldg(v + N + 1);
         v100 = (T)__ldg(v + NN); v101 = (T)__ldg(v + NN + 1); v110 = (T)__ldg(v + NN + N);
@@ -257,14 +269,57 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     const int ka = kk, kb = kk ? np - kk : half;
     const typename Vec2<T>::type pa = ld2(PH + 2 * ka), pb = ld2(PH + 2 * kb);
     T va[4], vb[4];
+    if constexpr (TEX) {
+      // the item's eight samples (a_0, b_0, a_1, b_1, ...) in batches of GB:
+      // both gathers of every sample of a batch are issued before the first
+      // is combined; a point outside the box (or of a padding ring) gathers
+      // at the origin and then takes the bounds-checked path (or zero)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + u;
-      va[u] = T(0); vb[u] = T(0);
-      if (r < R) {
-        const T rho = RH[r], pz = RZ[r];
-        va[u] = sample(c0 + rho * pa.x, c0 + rho * pa.y, pz);
-        vb[u] = sample(c0 + rho * pb.x, c0 + rho * pb.y, pz);
+      for (int sq = 0; sq < 8; sq += GB) {
+        float4 q0[GB], q1[GB];
+        T ftx[GB], fty[GB], ftz[GB];
+        bool in[GB];
+#pragma unroll
+        for (int v = 0; v < GB; ++v) {
+          const int u = (sq + v) >> 1, r = r0 + u;
+          const typename Vec2<T>::type pc = ((sq + v) & 1) ? pb : pa;
+          const T rho = r < R ? RH[r] : T(0), pz = r < R ? RZ[r] : T(-1);
+          const T px = c0 + rho * pc.x, py = c0 + rho * pc.y;
+          in[v] = px >= T(0) && py >= T(0) && pz >= T(0) && px <= hi && py <= hi && pz <= hi;
+          const int i = in[v] ? min((int)floor(px), N - 2) : 0;
+          const int j = in[v] ? min((int)floor(py), N - 2) : 0;
+          const int k = in[v] ? min((int)floor(pz), N - 2) : 0;
+          ftx[v] = px - (T)i; fty[v] = py - (T)j; ftz[v] = pz - (T)k;
+          const float tx0 = (float)i + 1.f, ty0 = yoff + (float)(k * N + j) + 1.f;
+          q0[v] = tex2Dgather<float4>(tob, tx0, ty0, 0);
+          q1[v] = tex2Dgather<float4>(tob, tx0, ty0 + (float)N, 0);
+        }
+#pragma unroll
+        for (int v = 0; v < GB; ++v) {
+          const int u = (sq + v) >> 1, r = r0 + u;
+          T val = combine(q0[v], q1[v], ftx[v], fty[v], ftz[v]);
+          if (!in[v]) {
+            val = T(0);
+            if (r < R) {
+              const typename Vec2<T>::type pc = ((sq + v) & 1) ? pb : pa;
+              const T rho = RH[r];
+              val = sample(c0 + rho * pc.x, c0 + rho * pc.y, RZ[r]);
+            }
+          }
+          if ((sq + v) & 1) vb[u] = val;
+          else va[u] = val;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        va[u] = T(0); vb[u] = T(0);
+        if (r < R) {
+          const T rho = RH[r], pz = RZ[r];
+          va[u] = sample(c0 + rho * pa.x, c0 + rho * pa.y, pz);
+          vb[u] = sample(c0 + rho * pb.x, c0 + rho * pb.y, pz);
+        }
       }
     }
     if (kk == 0) {
