@@ -160,8 +160,10 @@ __device__ __forceinline__ void st4(T *p, const T (&v)[4]) {
 // eight-load path, and the gathers go through the texture pipe, which serves
 // the 2x2 footprints faster than eight scattered loads.
 constexpr int ANALYZE_THREADS = 192;
-// samples whose texture gathers are in flight together (per thread)
-template <typename T> struct GatherBatch { static constexpr int value = sizeof(T) == 4 ? 2 : 2; };
+// samples whose texture gathers are in flight together (per thread): two
+// keep the kernel within four CTAs per SM; four need 95 registers (three
+// CTAs per SM) or spill under a four-CTA bound, and both measure slower
+constexpr int GATHER_BATCH = 2;
 
 template <typename T, int G, bool TEX>
 __global__ void __launch_bounds__(ANALYZE_THREADS)
@@ -170,7 +172,7 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
            const T *__restrict__ dcs, int Mp, int Qf, int Mq, const T *__restrict__ ptabT,
            const int *__restrict__ leg, const T *__restrict__ ring, T *__restrict__ out,
            const __grid_constant__ TexArgs ta) {
-  constexpr int GB = GatherBatch<T>::value;
+  constexpr int GB = GATHER_BATCH;
   const int s0 = blockIdx.x * G;
   const long b = blockIdx.y;
   const int Gs = G;  // the launcher picks G dividing S
@@ -219,27 +221,20 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
     T b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
     return b0 + tz * (b1 - b0);
   };
-  // trilinear at (px, py, pz); corners clamped so that all eight are in the box
-  // when the point is (the value is unchanged), bounds-checked otherwise
+  // trilinear at (px, py, pz) by plain loads (the load path, and points the
+  // texture path finds outside the box); corners clamped so that all eight
+  // are in the box when the point is (the value is unchanged), bounds-checked
+  // otherwise
   auto sample = [&](T px, T py, T pz) -> T {
     T fx = floor(px), fy = floor(py), fz = floor(pz);
     bool inside = px >= T(0) && py >= T(0) && pz >= T(0) && px <= hi && py <= hi && pz <= hi;
     if (inside) {
       int i = min((int)fx, N - 2), j = min((int)fy, N - 2), k = min((int)fz, N - 2);
       T tx = px - (T)i, ty = py - (T)j, tz = pz - (T)k;
-      if (TEX) {
-        const float tx0 = (float)i + 1.f, ty0 = yoff + (float)(k * N + j) + 1.f;
-        const float4 q0 = tex2Dgather<float4>(tob, tx0, ty0, 0);
-        const float4 q1 = tex2Dgather<float4>(tob, tx0, ty0 + (float)N, 0);
-        return combine(q0, q1, tx, ty, tz);
-      }
-      T v000, v001, v010, v011, v100, v101, v110, v111;
-      {
-        const float *v = vol + ((long)k * N + j) * N + i;
-        v000 = (T)__ldg(v); v001 = (T)__ldg(v + 1); v010 = (T)__ldg(v + N); v011 = (T)__ldg(v + N + 1);
-        v100 = (T)__ldg(v + NN); v101 = (T)__ldg(v + NN + 1); v110 = (T)__ldg(v + NN + N);
-        v111 = (T)__ldg(v + NN + N + 1);
-      }
+      const float *v = vol + ((long)k * N + j) * N + i;
+      const T v000 = (T)__ldg(v), v001 = (T)__ldg(v + 1), v010 = (T)__ldg(v + N),
+              v011 = (T)__ldg(v + N + 1), v100 = (T)__ldg(v + NN), v101 = (T)__ldg(v + NN + 1),
+              v110 = (T)__ldg(v + NN + N), v111 = (T)__ldg(v + NN + N + 1);
       T a00 = v000 + tx * (v001 - v000), a01 = v010 + tx * (v011 - v010);
       T a10 = v100 + tx * (v101 - v100), a11 = v110 + tx * (v111 - v110);
       T b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
