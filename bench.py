@@ -595,6 +595,39 @@ def time_refine_study(st, n=128):
     return out
 
 
+def host_cpu():
+    """Model name of the host CPU from /proc/cpuinfo (Arm hosts give implementer
+    and part codes instead of a name), else the platform's processor string."""
+    import platform
+    name, impl, part = "", "", ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k == "model name" and not name:
+                name = v
+            elif k == "CPU implementer" and not impl:
+                impl = v
+            elif k == "CPU part" and not part:
+                part = v
+    except OSError:
+        pass
+    if name:
+        return name
+    if impl or part:
+        return "%s (implementer %s, part %s)" % (platform.machine(), impl or "?", part or "?")
+    return platform.processor() or platform.machine()
+
+
+def oracle_per_core(oracle, pc, tc, kw, n=3):
+    """The oracle on one host thread, on the first n particles: the per-core rate."""
+    t0 = time.perf_counter()
+    oracle.align_batch(pc[:n], tc[:n] if tc.shape[0] == pc.shape[0] else tc, n_threads=1, **kw)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1,
+            "sample": "first %d particles of the batch, one thread, %.1f s" % (n, dt)}
+
+
 def run_reference(args):
     """The oracle (FP64 C, all host cores) on a bounded sample of the workload."""
     ws, rank, _ = dist_env()
@@ -624,7 +657,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(w, w.B, 1),
         "timed_sample_per_step": n,
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -977,7 +1011,9 @@ def main():
         tcpu = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": nb / tcpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": "first %d particles of the batch, FP64 C oracle, %.1f s"
-                                         % (nb, tcpu)}
+                                         % (nb, tcpu),
+                               "cpu": host_cpu(),
+                               "per_core": oracle_per_core(oracle, pc, tc, kw)}
         # the metric's accuracy gate: the oracle on every particle of the batch
         # (the rest of the batch, untimed), against every path's rotations
         if not args.no_oracle_gate and nb < B:

@@ -1,5 +1,5 @@
 """Host-side helpers of bench.py: the per-kernel roofline arithmetic, the L2
-note, and the kernel count of a step (no GPU needed)."""
+note, the kernel count of a step and the CPU-baseline helpers (no GPU needed)."""
 import math
 
 import bench
@@ -34,3 +34,14 @@ def test_kernel_roofline_arithmetic():
     assert r16["contraction"]["bound"] == "tensor"
     assert math.isclose(r32["contraction"]["peak"], r16["contraction"]["peak"] * 1.1 / 2.25,
                         rel_tol=1e-12)
+
+
+def test_cpu_baseline_per_core_and_host_model():
+    import oracle
+    assert isinstance(bench.host_cpu(), str) and bench.host_cpu()
+    w = synth.WORKLOADS["small32"]
+    d = synth.make_batch(w, B=2)
+    kw = dict(S=w.n_shells, r_max=w.r_max, L0=w.L0, K=w.K, P=w.P, M_iter=w.M_iter,
+              L_sched=w.L_sched)
+    r = bench.oracle_per_core(oracle, d["particles"].numpy(), d["templates"].numpy(), kw, n=1)
+    assert r["cores"] == 1 and r["value"] > 0 and "one thread" in r["sample"]
