@@ -615,7 +615,11 @@ def host_cpu():
     if name:
         return name
     if impl or part:
-        return "%s (implementer %s, part %s)" % (platform.machine(), impl or "?", part or "?")
+        arm = {"0xd0c": "Neoverse N1", "0xd40": "Neoverse V1", "0xd49": "Neoverse N2",
+               "0xd4f": "Neoverse V2"}
+        core = arm.get(part, "") if impl == "0x41" else ""
+        return "%s (implementer %s, part %s%s)" % (platform.machine(), impl or "?", part or "?",
+                                                   ": " + core if core else "")
     return platform.processor() or platform.machine()
 
 
