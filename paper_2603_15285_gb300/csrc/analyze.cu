@@ -6,9 +6,12 @@
 // equispaced in phi) and analyses every shell:
 //   F_m(s, j)  = sum_k f(r_s w_jk) exp(-i m phi_k)                 (phi DFT)
 //   f_lm(r_s)  = sum_j w_j (2 pi / n_phi) Pbar_lm(x_j) F_m(s, j)    (Legendre)
-// One CTA owns one (volume, shell): it gathers the n_theta * n_phi trilinear
-// samples into shared memory, folds the real DFT (pairs k, n_phi - k) and
-// runs the Legendre sums against the plan's table.
+// The shell-group kernel (k_analyze2) gives one CTA a volume and G shells: it
+// samples the G * n_theta rings into shared memory (texture gathers where the
+// batch allows), folds the real DFT (pairs k, n_phi - k) and runs the Legendre
+// sums against the plan's table.  The ring-batched kernel (k_analyze) takes
+// one shell per CTA a few rings at a time, for bandwidths whose shell does not
+// fit in shared memory.
 #include <stdlib.h>
 #include <algorithm>
 #include <type_traits>
