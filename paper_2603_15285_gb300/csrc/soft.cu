@@ -6,13 +6,26 @@
 //   S_mn(beta_k)   = sum_{l=max(|m|,|n|)}^{L0} c^l_{mn} d^l_{mn}(beta_k)   (beta transform)
 //   C(a_i,b_k,g_j) = Re sum_{m,n} S_mn(beta_k) e^{i(m a_i + n g_j)}       (2-D DFT)
 // For real volumes S_{-m,-n} = conj(S_mn), so the alpha sum folds to
-// m >= 0.  One CTA per (beta_k, particle).
+// m >= 0.
 //
 // Candidates: a grid point is a local maximum when it precedes all 26
 // neighbours in the order (value desc, index asc), alpha and gamma wrapping
 // and beta neighbours outside the grid skipped; the P strongest local maxima
-// in that order are kept.  One CTA per particle compacts the local maxima
-// into shared memory and selects P of them by P block-wide argmax rounds.
+// in that order are kept.
+//
+// Kernels (the launcher picks one by plan and tuning; all give the same
+// candidates):
+//   k_soft_grid + k_topk  grids too large for shared memory: one CTA per
+//                         (beta_k, particle) writes the grid, then one CTA per
+//                         particle compacts its local maxima and selects P of
+//                         them by block-wide argmax rounds;
+//   k_soft_fused, k_soft_stream, k_soft_chunk
+//                         one CTA per particle, the grid kept on chip (whole,
+//                         streamed by beta slice, or in passes of beta
+//                         slices with a ring of two neighbour slices);
+//   k_soft_warps          the chunked passes with a warp per beta slice;
+//   k_soft_tile           the chunked passes register-tiled for L0 = 8,
+//                         K = 2 in 32-bit plans (the bench configuration).
 #include <algorithm>
 #include <float.h>
 #include <limits.h>
