@@ -169,7 +169,14 @@ matcha_status matcha_workspace_size(matcha_plan plan, int B, size_t *bytes);
 
 /* a1+a2: shell sampling and SH analysis (Appendix A.1 with radial shells in
  * place of the radial Bessel basis).  vols_dev: B float32 volumes; coeffs_dev:
- * B * coeff_count complex reals, layout above. */
+ * B * coeff_count complex reals, layout above.  Samples are trilinear with
+ * zero outside the box.  A batch whose base address and row pitch meet the
+ * device's texture alignment rules is read through 2-D texture views of its
+ * buffer, created on first use and cached in the plan (up to 16 buffers);
+ * replacing a cached view synchronises the device first, and no view is
+ * created while `stream` is being captured.  Batches without a view are read
+ * with plain loads; the coefficients are bit-identical either way.  The same
+ * holds for the analysis inside matcha_align. */
 matcha_status matcha_analyze(matcha_plan plan, const float *vols_dev, int B, void *coeffs_dev,
                              void *stream);
 

@@ -531,8 +531,9 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
       };
       auto kern = tex ? pick(std::true_type{}) : pick(std::false_type{});
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      // 192 threads: six warps per CTA keep more CTAs resident than eight
-      // (measured 1.44 against 1.53 ms per 1,024 batch64 particles; 128: 1.68)
+      // 192 threads: six warps per CTA keep four CTAs resident per SM
+      // (measured 1.27 ms per 1,024 batch64 particles against 1.41 with 256
+      // threads and 1.59 with 128)
       kern<<<dim3(p.S / G, B), ANALYZE_THREADS, smem, st>>>(vols, p.N, p.S, p.LJ, p.rs, p.xj,
                                                 (const T *)p.phi_cs, (const T *)p.dft_cs, p.Mp,
                                                 p.Qf, p.Mq, (const T *)p.ptab_leg, p.leg_lm,
