@@ -175,3 +175,31 @@ def test_rotation_angle_and_chart():
     assert abs(O.rotation_angle(np.eye(3), O.euler_to_matrix(0, 0.37, 0)) - 0.37) < 1e-14
     # r_z(pi) r_y(b) r_z(pi) = r_y(-b)
     assert np.abs(O.euler_to_matrix(math.pi, 0.4, math.pi) - O.euler_to_matrix(0, -0.4, 0)).max() < 1e-15
+
+
+@pytest.mark.parametrize("b", [0.05, 0.7, 1.9, 3.0])
+def test_beta_derivatives_satisfy_the_degree_identity_and_the_differential_equation(b):
+    """Exact identities of the Wigner functions (from their Jacobi-polynomial
+    form), far tighter than finite differences:
+      sin b d'^l_mn = (l cos b - mn/l) d^l_mn - sqrt((l^2-m^2)(l^2-n^2))/l d^{l-1}_mn,
+      d''^l_mn = -cot b d'^l_mn + ((m^2 + n^2 - 2mn cos b)/sin^2 b - l(l+1)) d^l_mn."""
+    L = 20
+    d, d1, d2 = O.wigner_d_derivs(L, b)
+    s, c = math.sin(b), math.cos(b)
+    worst1 = worst2 = 0.0
+    for l in range(1, L + 1):
+        D = O.wigner_d_matrix(l, b, d)
+        D1 = O.wigner_d_matrix(l, b, d1)
+        D2 = O.wigner_d_matrix(l, b, d2)
+        Dm = O.wigner_d_matrix(l - 1, b, d)
+        for m in range(-l, l + 1):
+            for n in range(-l, l + 1):
+                prev = Dm[m + l - 1, n + l - 1] if max(abs(m), abs(n)) <= l - 1 else 0.0
+                q = math.sqrt((l * l - m * m) * (l * l - n * n))
+                rhs1 = (l * c - m * n / l) * D[m + l, n + l] - q / l * prev
+                worst1 = max(worst1, abs(s * D1[m + l, n + l] - rhs1))
+                Q = (m * m + n * n - 2 * m * n * c) / (s * s)
+                rhs2 = -c / s * D1[m + l, n + l] + (Q - l * (l + 1)) * D[m + l, n + l]
+                worst2 = max(worst2, abs(D2[m + l, n + l] - rhs2) * s * s)
+    assert worst1 < 1e-12
+    assert worst2 < 1e-12
