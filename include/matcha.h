@@ -175,8 +175,10 @@ matcha_status matcha_workspace_size(matcha_plan plan, int B, size_t *bytes);
  * buffer, created on first use and cached in the plan (up to 16 buffers);
  * replacing a cached view synchronises the device first, and no view is
  * created while `stream` is being captured.  Batches without a view are read
- * with plain loads; the coefficients are bit-identical either way.  The same
- * holds for the analysis inside matcha_align. */
+ * with plain loads; the coefficients are bit-identical either way.  The view
+ * lookup and the launch that uses it run under a per-plan lock, so host
+ * threads sharing a plan take turns there.  The same holds for the analysis
+ * inside matcha_align. */
 matcha_status matcha_analyze(matcha_plan plan, const float *vols_dev, int B, void *coeffs_dev,
                              void *stream);
 

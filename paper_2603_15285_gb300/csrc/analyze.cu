@@ -439,7 +439,8 @@ k_analyze2(const float *__restrict__ vols, int N, int S, int L,
 // height, more than TEX_MAX views) or when a new view would have to be made
 // while `st` is being captured into a graph; the kernel then reads the
 // volumes with plain loads.  Evicting a view synchronises the device first
-// (a kernel still queued may use it).
+// (a kernel still queued may use it).  The caller holds p.tex_mu through the
+// launch that uses the views.
 bool texture_views(const Plan &p, const float *vols, int B, cudaStream_t st, TexArgs &ta) {
   ta.vpt = 1;
   int dev = 0, pitch_al = 0, tex_al = 0, max_w = 0, max_h = 0, max_pitch = 0;
@@ -522,6 +523,7 @@ cudaError_t launch_analyze(const Plan &p, const float *vols, int B, T *coef, cud
     while (G > 1 && (p.S % G != 0 || analyze2_smem<T>(p, G) > 100 * 1024)) G >>= 1;
     size_t smem = analyze2_smem<T>(p, G);
     if (smem <= 200 * 1024) {
+      std::lock_guard<std::mutex> lock(p.tex_mu);
       TexArgs ta;
       const bool tex = texture_views(p, vols, B, st, ta);
       auto pick = [&](auto tag) {

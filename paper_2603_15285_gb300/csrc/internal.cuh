@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
 #include <vector>
 #include "../../include/matcha.h"
 
@@ -86,6 +87,9 @@ struct Plan {
   static constexpr int NTEXSET = 16;
   mutable TexSet texsets[NTEXSET];
   mutable unsigned long long tex_clock = 0;
+  // held from the view lookup through the analysis launch, so that a view
+  // another host thread evicts is never one whose launch is still to come
+  mutable std::mutex tex_mu;
 };
 void destroy_texsets(Plan &p);
 
