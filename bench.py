@@ -250,7 +250,7 @@ def measure_fp32_peak(st, local, reps=5):
     return out
 
 
-def survey_newton_units(w, B, newton_ms, peak):
+def wigner_term_units(w, B, newton_ms, peak):
     """Newton's work in Wigner terms, 3 P sum_j T(L_j) per particle with
     T(L) = (L+1)(2L+1)(2L+3)/3, at 30 flops per term (the per-unit figure of
     the path's roofline table), against the ALU peak."""
@@ -897,10 +897,10 @@ def main():
                                     if is32 else
                                     "%d SMs x 2 FP64 lanes x 2 x %.0f MHz (derived)" % (SMS, clk),
                      "flops_per_launch": newton_flops,
-                     # the same launch in the survey's algorithmic unit: 3 P sum_j T(L_j)
+                     # the same launch in the path's algorithmic unit: 3 P sum_j T(L_j)
                      # Wigner terms per particle (three evaluations per level) at 30 flops
                      # per term, against the same peak
-                     "survey_units": survey_newton_units(w, B, stage_ms["newton"], peak)},
+                     "wigner_term_units": wigner_term_units(w, B, stage_ms["newton"], peak)},
         "fp32_peak_probe": fp32_meas,
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,

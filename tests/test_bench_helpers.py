@@ -45,3 +45,12 @@ def test_cpu_baseline_per_core_and_host_model():
               L_sched=w.L_sched)
     r = bench.oracle_per_core(oracle, d["particles"].numpy(), d["templates"].numpy(), kw, n=1)
     assert r["cores"] == 1 and r["value"] > 0 and "one thread" in r["sample"]
+
+
+def test_wigner_term_units_of_the_bench_workload():
+    w = synth.WORKLOADS["batch64"]
+    r = bench.wigner_term_units(w, 1024, 2.0, 80.0)
+    # 3 P sum_j T(L_j), T(L) = (L+1)(2L+1)(2L+3)/3, L = 8, 16, 24, 32, P = 16
+    assert r["wigner_terms_per_particle"] == 3 * 16 * (969 + 6545 + 20825 + 47905) == 3659712
+    assert math.isclose(r["achieved"], 30.0 * 3659712 * 1024 / 2e-3 / 1e12, rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / 80.0, rel_tol=1e-12)
