@@ -263,8 +263,9 @@ def wigner_term_units(w, B, newton_ms, peak):
 
 def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
     """Achieved fraction of each step's bound, from the event-timed stages and
-    the algorithmic work per particle (volume bytes for the analysis, 8 S T(L)
-    flops for the contraction, grid points for the SOFFT search)."""
+    the algorithmic work per particle (volume bytes for the analysis, with its
+    dense DFT and Legendre flops beside them, 8 S T(L) flops for the
+    contraction, grid points for the SOFFT search)."""
     pk = measured_peaks()
     hbm = pk["hbm_gbs"]
     L, S, N = w.L_sched[-1], w.n_shells, w.N
@@ -273,6 +274,13 @@ def kernel_roofline(w, B, prec, stage_ms, alu_peak, m):
     out = {"analysis": {"kernel": "k_analyze2 (x2)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
                         "achieved": vol_bytes / (stage_ms["analyze"] * 1e-3) / 1e9}}
     out["analysis"]["frac"] = out["analysis"]["achieved"] / hbm
+    # the same launches in flops: per volume and shell, the phi DFT of n_theta
+    # rings of n_phi real samples to L+1 orders and the Legendre sums of n_lm
+    # coefficients over n_theta nodes, 4 flops per complex multiply-add
+    nt, nphi, nlm_a = L + 1, 2 * L + 2, (L + 1) * (L + 2) // 2
+    an_flops = 2.0 * S * (4 * nt * nphi * (L + 1) + 4 * nlm_a * nt) * B
+    out["analysis"]["flops_per_particle"] = an_flops / B
+    out["analysis"]["alu_frac"] = an_flops / (stage_ms["analyze"] * 1e-3) / 1e12 / alu_peak
     flops = 8.0 * S * T * B
     if prec in (m.TF32, m.BF16):
         tpk = pk["bf16_tflops"] * (1.0 if prec == m.BF16 else 1.1 / 2.25)

@@ -22,6 +22,11 @@ def test_kernel_roofline_arithmetic():
     want = 2 * 4 * 64 ** 3 * B / 2e-3 / 1e9
     assert math.isclose(r["analysis"]["achieved"], want, rel_tol=1e-12)
     assert math.isclose(r["analysis"]["frac"], want / peaks["hbm_gbs"], rel_tol=1e-12)
+    # and in flops: 32 shells x (33 rings x 66 samples x 33 orders + 561 (l, m) x 33 nodes)
+    # complex multiply-adds of 4 flops, two volumes: 23.1 MFLOP per particle
+    assert r["analysis"]["flops_per_particle"] == 2 * 32 * 4 * (33 * 66 * 33 + 561 * 33)
+    assert math.isclose(r["analysis"]["alu_frac"],
+                        r["analysis"]["flops_per_particle"] * B / 2e-3 / 1e12 / 80.0, rel_tol=1e-12)
     # contraction: 8 S T(L) flops per particle, T(32) = 47,905
     T = 33 * 65 * 67 // 3
     assert T == 47905
